@@ -1,0 +1,200 @@
+/*
+ * spider.h -- C ABI of the GB300-native SPIDER sampling step.
+ *
+ * SPIDER (Ross, Wilding, Azizzadenesheli, Kato; arXiv 2508.12117) samples the
+ * joint posterior of M hypocentres theta_m = (x_m, y_m, z_m, t0_m) (Sec. 2.1:
+ * theta = {(x_m, t_m^s)}) from N double-difference (dd) times with Stochastic
+ * Gradient Langevin Dynamics (Sec. 3.2).  One step of this library:
+ *
+ *   1. draws a minibatch of whole observation blocks (Eq. sgd: n of N),
+ *   2. evaluates travel times T(x_event; s_station) and dT/dx for every
+ *      (event, station) pair the minibatch touches (Sec. 2.1, Eq. forwardmodel),
+ *   3. forms residuals r_n = tau_obs_n - [(T_ik + t0_i) - (T_jk + t0_j)] (Eq. 1),
+ *   4. whitens them with the marginal covariance of each station group,
+ *      Sigma_g = sigma^2 I + kappa^2 W^1/2 A A^T W^1/2 (Eq. marginal_sigma),
+ *   5. scatter-reduces dlogp/dT onto pairs and chains it to the events,
+ *   6. adds the event and centroid priors (Sec. 3.1) and applies
+ *      theta += eps * grad + sqrt(2 eps) * eta (Sec. 3.2).
+ *
+ * Conventions (every entry point):
+ *   - returns SPIDER_OK (0) or a negative SPIDER_E_* code; the message of the
+ *     last failure on a context is spider_last_error(ctx) (a static string for
+ *     ctx == NULL failures);
+ *   - the caller owns every pointer it passes; the library reads host inputs
+ *     only during the call and copies what it keeps;
+ *   - the context owns all device memory it allocates; spider_destroy frees it;
+ *   - event order in every result is the caller's order (the library's own
+ *     spatial renumbering is undone);
+ *   - a context is not thread safe; distinct contexts are independent;
+ *   - device work runs on the context's CUDA stream (the `stream` argument of
+ *     spider_create, a cudaStream_t, or a private stream when NULL); calls that
+ *     return host data synchronise that stream.
+ */
+#ifndef SPIDER_H
+#define SPIDER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SPIDER_OK = 0,
+  SPIDER_E_INVAL = -1,       /* bad argument or inconsistent input               */
+  SPIDER_E_OOM = -2,         /* device or host allocation failed                 */
+  SPIDER_E_CUDA = -3,        /* a CUDA call failed (message holds its string)    */
+  SPIDER_E_NONFINITE = -4,   /* a NaN/Inf appeared in the state or the gradient  */
+  SPIDER_E_TIMEOUT = -5,     /* a bounded device-side wait gave up               */
+  SPIDER_E_UNSUPPORTED = -6  /* valid request this build cannot serve            */
+};
+
+/* travel-time model T(x; s) */
+enum {
+  SPIDER_TT_HOMOGENEOUS = 0,     /* T = |x - s| / v0 (Sec. 2.1, homogeneous medium) */
+  SPIDER_TT_LINEAR_GRADIENT = 1, /* v = v0 + g z: T = arccosh(1 + g^2 r^2 / (2 v_x v_s)) / g */
+  SPIDER_TT_MLP = 2              /* T = |x - s| * tau(x, s), tau an MLP 6 -> 4 x H SiLU -> 1
+                                    (the EikoNet stand-in of Sec. 3.2) */
+};
+
+/* arithmetic of the MLP hidden layers (layer 1, output layer, T, residuals
+ * and positions are FP32 in every mode) */
+enum { SPIDER_FP32 = 0, SPIDER_BF16 = 1, SPIDER_FP8 = 2 };
+
+typedef struct {
+  int64_t M;               /* events                                             */
+  int64_t N;               /* dd observations                                    */
+  const double *xyzt0;     /* M x 4 row-major initial catalog theta_0: x, y, z (km,
+                              z positive down), t0 (s).  Also the mean of the event
+                              prior (Sec. 3.1) and the centre of the centroid prior. */
+  const int32_t *i;        /* N: first event xi^1_n, in [0, M)                   */
+  const int32_t *j;        /* N: second event xi^2_n, in [0, M), != i            */
+  const int32_t *k;        /* N: station eta_n, in [0, S)                        */
+  const double *dt;        /* N: observed dd time tau_obs_n = t_i - t_j at k (s) */
+  const float *w;          /* N edge weights w_e of Eq. correlation_decay, already
+                              normalised; NULL: computed from theta_0 as
+                              (d_e / ell)^p + eps_w, mean 1 per station group     */
+} spider_catalog;
+
+typedef struct {
+  int32_t S;               /* stations                                           */
+  const double *xyz;       /* S x 3 row-major station positions (km)             */
+} spider_stations;
+
+typedef struct {
+  int32_t kind;            /* SPIDER_TT_*                                        */
+  double v0, g;            /* homogeneous speed / gradient medium (km/s, 1/s)    */
+  int32_t H;               /* MLP hidden width: a multiple of 32, 32..256        */
+  const float *W[5];       /* MLP weights, (out, in) row-major: H x 6, H x H (x3),
+                              1 x H.  Inputs are [x_src; x_rcv] in km.          */
+  const float *b[5];       /* MLP biases: H (x4), 1                              */
+} spider_net;
+
+typedef struct {
+  double sigma;            /* sigma_phi (s), iid noise of Eq. marginal_sigma     */
+  double kappa;            /* kappa_phi (s), shared-event term; 0 = iid likelihood */
+  double p, ell, eps_w;    /* Eq. correlation_decay exponent, length (km), floor  */
+  double sig_e[4];         /* event prior sigmas (km, km, km, s)                  */
+  double sig_c[4];         /* centroid prior sigmas (km, km, km, s)               */
+  int64_t batch_n;         /* observations per minibatch; 0 or >= N = full batch */
+  int64_t block_obs;       /* observations per minibatch block, 1..4096          */
+  int32_t precision;       /* SPIDER_FP32 / SPIDER_BF16 / SPIDER_FP8             */
+  int32_t thin;            /* keep every thin-th state as a sample (>= 1)        */
+  int32_t reorder;         /* 1: renumber events along a Morton curve (locality) */
+  int32_t chain;           /* Philox counter word 1 (chain id)                   */
+  int32_t catalog;         /* Philox counter word 2 (catalog id)                 */
+  float noise_scale;       /* multiplies sqrt(2 eps) eta (stage-3 ramp, Sec. 3.2) */
+  int32_t pcg_max_it;      /* whitening solve: iteration cap                     */
+  float pcg_tol;           /* whitening solve: relative residual target          */
+  int64_t sample_cap;      /* samples kept on the device (ring buffer)           */
+} spider_config;
+
+typedef struct spider_ctx spider_ctx;
+
+/* Fills *cfg with the defaults: Table 1 / Sec. 4 values (kappa 0.03 s, p 0.25,
+ * ell 40 km, centroid sigma 0.01), event prior 0.5 km / 0.1 s (Sec. 4.1),
+ * full batch, blocks of 4096, FP32, thin 1, reorder 1, noise 1, PCG 400 / 1e-6. */
+void spider_config_default(spider_config *cfg);
+
+/* Validates and copies the catalog, stations and network; builds the canonical
+ * observation order, the (event, station) pair table, the minibatch blocks and
+ * the edge weights; uploads everything; state theta := theta_0, step := 0.
+ * stream: a cudaStream_t or NULL.  *out receives the context on success. */
+int spider_create(const spider_catalog *cat, const spider_stations *sta,
+                  const spider_net *net, const spider_config *cfg, void *stream,
+                  spider_ctx **out);
+
+/* Gradient of the log posterior at the current state (Eq. sgd without the
+ * step): minibatch keyed by batch_seed (0 = full batch), likelihood scaled by
+ * N/n.  grad_out: host M x 4 FP32 (caller order) or NULL.  logpost_out: host
+ * FP64 log posterior estimate (constants dropped) or NULL.  Synchronous. */
+int spider_grad_logpost(spider_ctx *ctx, uint64_t batch_seed, float *grad_out,
+                        double *logpost_out);
+
+/* One SGLD step (Sec. 3.2): minibatch and Langevin noise both keyed by
+ * batch_seed; theta += eps * grad + noise_scale * sqrt(2 eps) * eta.  Asynchronous
+ * on the context stream; errors found on the device surface at the next
+ * synchronous call. */
+int spider_sgld_step(spider_ctx *ctx, float eps, uint64_t batch_seed);
+
+/* Copies up to `cap` stored samples (oldest first) as M x 4 FP64 each, caller
+ * order, into out; *n_written = count.  Synchronous. */
+int spider_samples(spider_ctx *ctx, double *out, int64_t cap, int64_t *n_written);
+
+/* Current state (M x 4 FP64, caller order) and step counter.  Synchronous. */
+int spider_get_state(spider_ctx *ctx, double *theta_out, int64_t *step_out);
+
+/* Replaces the state and step counter (exact resume: with the same per-step
+ * seeds the continued chain is bit-identical).  Synchronous. */
+int spider_set_state(spider_ctx *ctx, const double *theta, int64_t step);
+
+/* Waits for queued device work; returns the first device-side error, if any. */
+int spider_sync(spider_ctx *ctx);
+
+/* Per-stage device time of the most recent step or gradient, in ms, from CUDA
+ * events on the context stream (enable with spider_set_timing(ctx, 1)):
+ * out[0] selection+pair table, [1] travel times (the MLP), [2] residuals and
+ * whitening, [3] scatter and event reduce + update, [4] whole call.  Also the
+ * pairs evaluated (P_u), observations used and whitening iterations. */
+int spider_set_timing(spider_ctx *ctx, int enable);
+int spider_last_timing(spider_ctx *ctx, float out_ms[5], int64_t *pairs,
+                       int64_t *n_obs, int32_t *pcg_iters);
+
+/* Debug views of the last evaluation (synchronous):
+ * spider_debug_blocks: selected block ids in selection order (int64, cap);
+ * spider_debug_obs: for every observation of the last minibatch, its caller
+ * index, residual r_n and whitened q_n = (Sigma^-1 r)_n (unscaled). */
+int spider_debug_blocks(spider_ctx *ctx, int64_t *out, int64_t cap, int64_t *n);
+int spider_debug_obs(spider_ctx *ctx, int64_t *idx_out, float *r_out, float *q_out,
+                     int64_t cap, int64_t *n);
+
+const char *spider_last_error(const spider_ctx *ctx);
+void spider_destroy(spider_ctx *ctx);
+
+/* ---- context-free pieces (device pointers, caller-owned) ----------------- */
+
+typedef struct spider_netdev spider_netdev;
+
+/* Uploads a travel-time network (any kind) for spider_tt_pairs. */
+int spider_net_upload(const spider_net *net, int32_t precision, spider_netdev **out);
+void spider_net_free(spider_netdev *nd);
+
+/* Travel times and source Jacobians for P (source, receiver) pairs, the kernel
+ * a step uses (Sec. 2.1; reverse-mode chain of Sec. 3.2 for the MLP).
+ * src, rcv: device P x 4 FP32 (x, y, z, unused).  T_hi, T_lo: device P FP32
+ * each, T = T_hi + T_lo to about 1e-12 relative (T_lo may be NULL).
+ * J: device P x 4 FP32 (dT/dx, dT/dy, dT/dz, 0) or NULL.  stream: cudaStream_t
+ * or NULL (legacy default).  Asynchronous. */
+int spider_tt_pairs(const spider_netdev *nd, int64_t P, const float *src, const float *rcv,
+                    float *T_hi, float *T_lo, float *J, void *stream);
+
+/* Philox4x32-10 words computed on the device (host output, synchronous):
+ * out[4 m + a] = word a of Philox(counter (c0 + m, c1, c2, c3), key = seed),
+ * m in [0, n).  Exposed so the noise stream can be checked word for word. */
+int spider_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                        int64_t n, uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPIDER_H */

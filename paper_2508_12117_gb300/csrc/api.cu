@@ -1,0 +1,701 @@
+// C ABI of the library: context lifetime, uploads, step orchestration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "prep.h"
+#include "spider.h"
+
+using namespace spider;
+
+struct spider_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, num_sms = 0;
+  spider_config cfg{};
+  std::vector<int32_t> ev_old;     // internal event -> caller event
+  std::vector<int32_t> ord;        // canonical obs -> caller obs
+  std::vector<double> th0;         // M x 4 internal order
+  NetView net{};
+  StepView v{};
+  std::vector<void*> allocs;
+  float* tt_scratch = nullptr;
+  int gu = 0, pgrid = 0;
+  int tag = 0;
+  int cur = 0;                     // which centroid partial buffer holds the current state
+  int64_t step = 0;
+  int64_t n_samples = 0;           // samples written so far (ring of sample_cap)
+  int64_t last_nb = 0;
+  bool timing = false;
+  cudaEvent_t ev[6] = {};
+  float last_ms[5] = {0, 0, 0, 0, 0};
+  bool have_timing = false;
+};
+
+struct spider_netdev {
+  NetView net{};
+  std::vector<void*> allocs;
+  float* scratch = nullptr;
+  int num_sms = 0;
+};
+
+namespace {
+
+const char* g_static_err = "";
+
+int cuda_fail(spider_ctx* c, cudaError_t e, const char* what) {
+  if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  g_static_err = cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SPIDER_E_OOM : SPIDER_E_CUDA;
+}
+
+#define CK(ctx, call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(std::vector<void*>& list, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  list.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t dupload(std::vector<void*>& list, T** p, const T* src, size_t n, cudaStream_t st) {
+  cudaError_t e = dalloc(list, p, n);
+  if (e != cudaSuccess || n == 0) return e;
+  return cudaMemcpyAsync(*p, src, n * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+void split_df(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+bool finite_arr(const float* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// Validates a network description; returns 0 or an error code with msg.
+int check_net(const spider_net* net, int precision, std::string* msg) {
+  if (!net) { *msg = "null network"; return SPIDER_E_INVAL; }
+  if (net->kind == SPIDER_TT_HOMOGENEOUS) {
+    if (!(net->v0 > 0.0)) { *msg = "homogeneous medium needs v0 > 0"; return SPIDER_E_INVAL; }
+    return SPIDER_OK;
+  }
+  if (net->kind == SPIDER_TT_LINEAR_GRADIENT) {
+    if (!(net->v0 > 0.0) || !(net->g > 0.0)) { *msg = "gradient medium needs v0 > 0, g > 0"; return SPIDER_E_INVAL; }
+    return SPIDER_OK;
+  }
+  if (net->kind != SPIDER_TT_MLP) { *msg = "unknown travel-time kind"; return SPIDER_E_INVAL; }
+  const int H = net->H;
+  if (!tt_supported_width(H)) { *msg = "MLP width H must be 32, 64, 128 or 256"; return SPIDER_E_UNSUPPORTED; }
+  if (precision < SPIDER_FP32 || precision > SPIDER_FP8) { *msg = "unknown precision"; return SPIDER_E_INVAL; }
+  if (precision != SPIDER_FP32 && !mlp_tc_supported(H, precision)) {
+    *msg = "this precision / width has no tensor-core kernel in this build";
+    return SPIDER_E_UNSUPPORTED;
+  }
+  const size_t wn[5] = {(size_t)H * 6, (size_t)H * H, (size_t)H * H, (size_t)H * H, (size_t)H};
+  const size_t bn[5] = {(size_t)H, (size_t)H, (size_t)H, (size_t)H, 1};
+  for (int l = 0; l < 5; ++l) {
+    if (!net->W[l] || !net->b[l]) { *msg = "null MLP weight or bias"; return SPIDER_E_INVAL; }
+    if (!finite_arr(net->W[l], wn[l]) || !finite_arr(net->b[l], bn[l])) {
+      *msg = "non-finite MLP weight or bias";
+      return SPIDER_E_INVAL;
+    }
+  }
+  return SPIDER_OK;
+}
+
+// Uploads weights into a NetView (allocations appended to `list`).
+cudaError_t upload_net(const spider_net* in, int precision, NetView* nv, std::vector<void*>& list,
+                       cudaStream_t st) {
+  NetView n{};
+  n.kind = in->kind;
+  n.precision = precision;
+  n.H = in->H;
+  n.v0 = (float)in->v0;
+  n.g = (float)in->g;
+  if (in->v0 > 0.0) split_df(1.0 / in->v0, n.inv_v_hi, n.inv_v_lo);
+  cudaError_t e = cudaSuccess;
+  if (in->kind == SPIDER_TT_MLP) {
+    const int H = in->H;
+    float* p = nullptr;
+    if ((e = dupload(list, &p, in->W[0], (size_t)H * 6, st))) return e;
+    n.W1 = p;
+    if ((e = dupload(list, &p, in->b[0], (size_t)H, st))) return e;
+    n.b1 = p;
+    std::vector<float> t((size_t)H * H);
+    for (int l = 0; l < 3; ++l) {
+      const float* W = in->W[l + 1];
+      for (int o = 0; o < H; ++o)
+        for (int i = 0; i < H; ++i) t[(size_t)i * H + o] = W[(size_t)o * H + i];
+      if ((e = dupload(list, &p, t.data(), t.size(), st))) return e;
+      n.Wt[l] = p;
+      if ((e = dupload(list, &p, W, (size_t)H * H, st))) return e;
+      n.Wn[l] = p;
+      if ((e = dupload(list, &p, in->b[l + 1], (size_t)H, st))) return e;
+      n.bh[l] = p;
+    }
+    if ((e = dupload(list, &p, in->W[4], (size_t)H, st))) return e;
+    n.W5 = p;
+    n.b5 = in->b[4][0];
+    if (precision != SPIDER_FP32) {
+      void* img = nullptr;
+      float* sc = nullptr;
+      const float* Wn_host[3] = {in->W[1], in->W[2], in->W[3]};
+      if ((e = mlp_tc_prepare(Wn_host, H, precision, &img, &sc, st))) return e;
+      if (img) list.push_back(img);
+      if (sc) list.push_back(sc);
+      n.tc = img;
+      n.tc_scale = sc;
+    }
+    // the transposed copy above must outlive the async copy
+    if ((e = cudaStreamSynchronize(st))) return e;
+  }
+  *nv = n;
+  return cudaSuccess;
+}
+
+void free_all(std::vector<void*>& list) {
+  for (void* p : list) cudaFree(p);
+  list.clear();
+}
+
+int check_device_error(spider_ctx* c) {
+  int32_t e = 0;
+  cudaError_t ce = cudaMemcpyAsync(&e, c->v.counters + kCntError, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                   c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "device error check");
+  if (e != 0) {
+    cudaMemsetAsync(c->v.counters + kCntError, 0, sizeof(int32_t), c->stream);
+    cudaStreamSynchronize(c->stream);
+    c->err = e == SPIDER_E_NONFINITE ? "non-finite value in the state or gradient"
+             : e == SPIDER_E_TIMEOUT ? "a bounded device-side wait timed out"
+                                     : "device-side error";
+    return e;
+  }
+  return SPIDER_OK;
+}
+
+// One evaluation of the gradient (mode 0) or one SGLD step (mode 1).
+int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
+  const spider_config& cfg = c->cfg;
+  StepView& v = c->v;
+  const bool batch_full = cfg.batch_n <= 0 || cfg.batch_n >= v.N;
+  const bool full = batch_full || (mode == 0 && seed == 0);
+  const int64_t n_b = full ? v.NB : std::min<int64_t>(v.NB, (cfg.batch_n + v.B - 1) / v.B);
+  const int tag = ++c->tag;
+  cudaStream_t st = c->stream;
+  if (c->timing) CK(c, cudaEventRecord(c->ev[0], st));
+  CK(c, cudaMemsetAsync(v.counters, 0, 3 * sizeof(int32_t), st));
+  CK(c, cudaMemsetAsync(v.counters + kCntBarArrive, 0, 2 * sizeof(int32_t), st));
+  CK(c, launch_select(v, n_b, full ? 1 : 0, seed, tag, st));
+  if (c->timing) CK(c, cudaEventRecord(c->ev[1], st));
+  PairSource src{};
+  src.uniq_pair = v.uniq_pair;
+  src.pair_ev = v.pair_ev;
+  src.pair_st = v.pair_st;
+  src.th0_hi = v.th0_hi;
+  src.th0_lo = v.th0_lo;
+  src.dth = v.dth;
+  src.sta_hi = v.sta_hi;
+  src.sta_lo = v.sta_lo;
+  src.n_dev = v.counters + kCntPairs;
+  src.n_host = v.P;
+  TTOut out{v.T2, v.J};
+  CK(c, launch_tt(c->net, src, out, c->num_sms, c->tt_scratch, st));
+  if (c->timing) CK(c, cudaEventRecord(c->ev[2], st));
+  CK(c, launch_resid(v, n_b, tag, c->gu, st));
+  CK(c, launch_pcg(v, tag, n_b, cfg.pcg_max_it, cfg.pcg_tol, c->pgrid, st));
+  if (c->timing) CK(c, cudaEventRecord(c->ev[3], st));
+  int64_t slot = -1;
+  if (mode == 1 && ((c->step + 1) % cfg.thin) == 0 && v.sample_cap > 0) slot = c->n_samples % v.sample_cap;
+  CK(c, launch_finish(v, n_b, tag, c->gu, mode, eps, cfg.noise_scale, seed, c->cur, slot, st));
+  if (c->timing) CK(c, cudaEventRecord(c->ev[4], st));
+  if (mode == 1) {
+    c->cur ^= 1;
+    c->step += 1;
+    if (slot >= 0) c->n_samples += 1;
+  }
+  c->last_nb = n_b;
+  c->have_timing = c->timing;
+  return SPIDER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void spider_config_default(spider_config* c) {
+  std::memset(c, 0, sizeof(*c));
+  c->sigma = 0.01;
+  c->kappa = 0.03;
+  c->p = 0.25;
+  c->ell = 40.0;
+  c->eps_w = 1e-5;
+  c->sig_e[0] = c->sig_e[1] = c->sig_e[2] = 0.5;
+  c->sig_e[3] = 0.1;
+  for (int a = 0; a < 4; ++a) c->sig_c[a] = 0.01;
+  c->batch_n = 0;
+  c->block_obs = 4096;
+  c->precision = SPIDER_FP32;
+  c->thin = 1;
+  c->reorder = 1;
+  c->chain = 0;
+  c->catalog = 0;
+  c->noise_scale = 1.0f;
+  c->pcg_max_it = 400;
+  c->pcg_tol = 1e-6f;
+  c->sample_cap = 16;
+}
+
+int spider_create(const spider_catalog* cat, const spider_stations* sta, const spider_net* net,
+                  const spider_config* cfg, void* stream, spider_ctx** out) {
+  if (!out) return SPIDER_E_INVAL;
+  *out = nullptr;
+  spider_ctx* c = new spider_ctx();
+  auto bail = [&](int code) {
+    g_static_err = "spider_create failed";
+    static thread_local std::string last;
+    last = c->err;
+    g_static_err = last.c_str();
+    free_all(c->allocs);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return code;
+  };
+  if (!cfg) { c->err = "null config"; return bail(SPIDER_E_INVAL); }
+  c->cfg = *cfg;
+  if (c->cfg.thin < 1 || c->cfg.pcg_max_it < 0 || !(c->cfg.pcg_tol >= 0.f) || c->cfg.sample_cap < 0 ||
+      !(c->cfg.noise_scale >= 0.f)) {
+    c->err = "need thin >= 1, pcg_max_it >= 0, pcg_tol >= 0, sample_cap >= 0, noise_scale >= 0";
+    return bail(SPIDER_E_INVAL);
+  }
+  int rc = check_net(net, cfg->precision, &c->err);
+  if (rc) return bail(rc);
+  Prep P;
+  rc = prepare(cat, sta, cfg, &P, &c->err);
+  if (rc) return bail(rc);
+
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device))) return bail(cuda_fail(c, e, "cudaGetDevice"));
+  if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device)))
+    return bail(cuda_fail(c, e, "device attribute"));
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking))) return bail(cuda_fail(c, e, "stream"));
+    c->own_stream = true;
+  }
+  cudaStream_t st = c->stream;
+  auto& L = c->allocs;
+  StepView& v = c->v;
+  v.M = P.M; v.N = P.N; v.S = P.S; v.NB = P.NB; v.B = P.B; v.P = P.P; v.Q = P.Q; v.L_max = P.L_max;
+  const size_t M = P.M, N = P.N, S = P.S, NB = P.NB, PP = P.P, Q = P.Q;
+
+  std::vector<float4> h_hi(M), h_lo(M);
+  for (size_t m = 0; m < M; ++m) {
+    float hx[4], lx[4];
+    for (int a = 0; a < 4; ++a) split_df(P.th0[4 * m + a], hx[a], lx[a]);
+    h_hi[m] = make_float4(hx[0], hx[1], hx[2], hx[3]);
+    h_lo[m] = make_float4(lx[0], lx[1], lx[2], lx[3]);
+  }
+  std::vector<float4> s_hi(S), s_lo(S);
+  for (size_t s = 0; s < S; ++s) {
+    float hx[3], lx[3];
+    for (int a = 0; a < 3; ++a) split_df(sta->xyz[3 * s + a], hx[a], lx[a]);
+    s_hi[s] = make_float4(hx[0], hx[1], hx[2], 0.f);
+    s_lo[s] = make_float4(lx[0], lx[1], lx[2], 0.f);
+  }
+#define UP(field, src, n)                                                       \
+  do {                                                                          \
+    decltype(v.field) _p;                                                       \
+    using _T = std::remove_const_t<std::remove_pointer_t<decltype(v.field)>>;   \
+    _T* _q = nullptr;                                                           \
+    if ((e = dupload(L, &_q, (const _T*)(src), (n), st))) return bail(cuda_fail(c, e, "upload " #field)); \
+    _p = _q;                                                                    \
+    v.field = _p;                                                               \
+  } while (0)
+#define AL(field, n)                                                            \
+  do {                                                                          \
+    using _T = std::remove_pointer_t<decltype(v.field)>;                        \
+    _T* _q = nullptr;                                                           \
+    if ((e = dalloc(L, &_q, (n)))) return bail(cuda_fail(c, e, "alloc " #field)); \
+    v.field = _q;                                                               \
+  } while (0)
+  UP(th0_hi, h_hi.data(), M);
+  UP(th0_lo, h_lo.data(), M);
+  UP(sta_hi, s_hi.data(), S);
+  UP(sta_lo, s_lo.data(), S);
+  UP(pair_ev, P.pair_ev.data(), PP);
+  UP(pair_st, P.pair_st.data(), PP);
+  UP(pair_off, P.pair_off.data(), M + 1);
+  UP(obs_l, P.obs_l.data(), N);
+  UP(obs_dt, P.obs_dt.data(), N);
+  UP(obs_sw, P.obs_sw.data(), N);
+  UP(blk_node_off, P.blk_node_off.data(), NB + 1);
+  UP(node_pair, P.node_pair.data(), Q);
+  UP(node_he, P.node_he.data(), Q);
+  UP(blk_he, P.blk_he.data(), 2 * N);
+  UP(inc_off, P.inc_off.data(), PP + 1);
+  UP(inc_q, P.inc_q.data(), Q);
+  UP(inc_b, P.inc_b.data(), Q);
+  AL(dth, M);
+  AL(sel, NB);
+  AL(blk_stamp, NB);
+  AL(owner_q, Q);
+  AL(multi, Q);
+  AL(loc2u, Q);
+  AL(blk_owner_cnt, NB);
+  AL(blk_owner_off, NB);
+  AL(uniq_pair, PP);
+  AL(uniq_q, PP);
+  AL(T2, PP);
+  AL(J, PP);
+  AL(r_obs, N);
+  AL(q_obs, N);
+  AL(part_a, Q);
+  AL(part_b, Q);
+  AL(rhs, PP);
+  AL(diag, PP);
+  AL(z, PP);
+  AL(res, PP);
+  AL(pv, PP);
+  AL(Ap, PP);
+  AL(yv, PP);
+  AL(s_u, PP);
+  AL(gp, PP);
+  AL(pstamp, PP);
+  AL(estamp, M);
+  AL(grad, M);
+  AL(counters, kCntSlots);
+  AL(red, 8 * kMaxGrid);
+  AL(dblk, NB);
+  AL(dred, 4 * kMaxGrid);
+  AL(dout, 8);
+  AL(cen_part, 2 * kMaxGrid);
+  const int64_t cap = c->cfg.sample_cap;
+  AL(samples, (size_t)std::max<int64_t>(cap, 1) * M);
+#undef UP
+#undef AL
+  v.sample_cap = cap;
+  if ((e = cudaMemsetAsync(v.dth, 0, M * sizeof(float4), st))) return bail(cuda_fail(c, e, "memset"));
+  if ((e = cudaMemsetAsync(v.blk_stamp, 0xFF, NB * sizeof(int32_t), st))) return bail(cuda_fail(c, e, "memset"));
+  if ((e = cudaMemsetAsync(v.pstamp, 0xFF, PP * sizeof(int32_t), st))) return bail(cuda_fail(c, e, "memset"));
+  if ((e = cudaMemsetAsync(v.estamp, 0xFF, M * sizeof(int32_t), st))) return bail(cuda_fail(c, e, "memset"));
+  if ((e = cudaMemsetAsync(v.counters, 0, kCntSlots * sizeof(int32_t), st))) return bail(cuda_fail(c, e, "memset"));
+  const double s2 = cfg->sigma * cfg->sigma;
+  v.whiten = cfg->kappa > 0.0 ? 1 : 0;
+  v.lam = v.whiten ? (float)(s2 / (cfg->kappa * cfg->kappa)) : 0.f;
+  v.inv_s2 = (float)(1.0 / s2);
+  v.inv_sig_e2 = make_float4((float)(1.0 / (cfg->sig_e[0] * cfg->sig_e[0])), (float)(1.0 / (cfg->sig_e[1] * cfg->sig_e[1])),
+                             (float)(1.0 / (cfg->sig_e[2] * cfg->sig_e[2])), (float)(1.0 / (cfg->sig_e[3] * cfg->sig_e[3])));
+  v.inv_sig_c2 = make_float4((float)(1.0 / (cfg->sig_c[0] * cfg->sig_c[0])), (float)(1.0 / (cfg->sig_c[1] * cfg->sig_c[1])),
+                             (float)(1.0 / (cfg->sig_c[2] * cfg->sig_c[2])), (float)(1.0 / (cfg->sig_c[3] * cfg->sig_c[3])));
+  v.cen_grid = (int)std::min<int64_t>((int64_t)(M + 255) / 256, (int64_t)std::min(kMaxGrid, 4 * c->num_sms));
+  v.chain = (uint32_t)cfg->chain;
+  v.catalog = (uint32_t)cfg->catalog;
+  c->gu = std::min(kMaxGrid, 4 * c->num_sms);
+
+  if ((e = upload_net(net, cfg->precision, &c->net, L, st))) return bail(cuda_fail(c, e, "network upload"));
+  const size_t scr = tt_scratch_floats(c->net, c->num_sms);
+  if (scr) {
+    if ((e = dalloc(L, &c->tt_scratch, scr))) return bail(cuda_fail(c, e, "alloc scratch"));
+  }
+  if ((e = configure_step_kernels(v))) return bail(cuda_fail(c, e, "kernel attributes"));
+  c->pgrid = pcg_grid(v, c->num_sms);
+  if (c->pgrid < 1) {
+    c->err = "whitening kernel does not fit on the device (block too large)";
+    return bail(SPIDER_E_UNSUPPORTED);
+  }
+  if ((e = launch_cen_init(v, 0, st))) return bail(cuda_fail(c, e, "centroid init"));
+  c->ev_old = std::move(P.ev_old);
+  c->ord = std::move(P.ord);
+  c->th0 = std::move(P.th0);
+  for (int i = 0; i < 6; ++i)
+    if ((e = cudaEventCreate(&c->ev[i]))) return bail(cuda_fail(c, e, "event"));
+  if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "create sync"));
+  *out = c;
+  return SPIDER_OK;
+}
+
+int spider_grad_logpost(spider_ctx* c, uint64_t batch_seed, float* grad_out, double* logpost_out) {
+  if (!c) return SPIDER_E_INVAL;
+  int rc = evaluate(c, batch_seed, 0, 0.f);
+  if (rc) return rc;
+  const size_t M = c->v.M;
+  std::vector<float4> g(grad_out ? M : 0);
+  double lp = 0.0;
+  if (grad_out) CK(c, cudaMemcpyAsync(g.data(), c->v.grad, M * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  if (logpost_out) CK(c, cudaMemcpyAsync(&lp, c->v.dout + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  rc = check_device_error(c);
+  if (rc) return rc;
+  if (grad_out)
+    for (size_t m = 0; m < M; ++m) {
+      float* o = grad_out + 4 * (size_t)c->ev_old[m];
+      o[0] = g[m].x; o[1] = g[m].y; o[2] = g[m].z; o[3] = g[m].w;
+    }
+  if (logpost_out) *logpost_out = lp;
+  return SPIDER_OK;
+}
+
+int spider_sgld_step(spider_ctx* c, float eps, uint64_t batch_seed) {
+  if (!c) return SPIDER_E_INVAL;
+  if (!(eps > 0.f) || !std::isfinite(eps)) {
+    c->err = "eps must be finite and > 0";
+    return SPIDER_E_INVAL;
+  }
+  return evaluate(c, batch_seed, 1, eps);
+}
+
+int spider_samples(spider_ctx* c, double* out, int64_t cap, int64_t* n_written) {
+  if (!c || !n_written || (cap > 0 && !out)) return SPIDER_E_INVAL;
+  CK(c, cudaStreamSynchronize(c->stream));
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  const int64_t have = std::min<int64_t>(c->n_samples, c->v.sample_cap);
+  const int64_t n = std::min<int64_t>(have, cap);
+  const int64_t first = c->n_samples - have;     // oldest kept sample index
+  const size_t M = c->v.M;
+  std::vector<float4> buf(M);
+  for (int64_t s = 0; s < n; ++s) {
+    const int64_t slot = (first + s) % c->v.sample_cap;
+    CK(c, cudaMemcpy(buf.data(), c->v.samples + slot * M, M * sizeof(float4), cudaMemcpyDeviceToHost));
+    double* o = out + (size_t)s * 4 * M;
+    for (size_t m = 0; m < M; ++m) {
+      double* x = o + 4 * (size_t)c->ev_old[m];
+      const double* t = &c->th0[4 * m];
+      x[0] = t[0] + (double)buf[m].x;
+      x[1] = t[1] + (double)buf[m].y;
+      x[2] = t[2] + (double)buf[m].z;
+      x[3] = t[3] + (double)buf[m].w;
+    }
+  }
+  *n_written = n;
+  return SPIDER_OK;
+}
+
+int spider_get_state(spider_ctx* c, double* theta_out, int64_t* step_out) {
+  if (!c) return SPIDER_E_INVAL;
+  const size_t M = c->v.M;
+  std::vector<float4> buf(M);
+  CK(c, cudaMemcpyAsync(buf.data(), c->v.dth, M * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  if (theta_out)
+    for (size_t m = 0; m < M; ++m) {
+      double* x = theta_out + 4 * (size_t)c->ev_old[m];
+      const double* t = &c->th0[4 * m];
+      x[0] = t[0] + (double)buf[m].x;
+      x[1] = t[1] + (double)buf[m].y;
+      x[2] = t[2] + (double)buf[m].z;
+      x[3] = t[3] + (double)buf[m].w;
+    }
+  if (step_out) *step_out = c->step;
+  return SPIDER_OK;
+}
+
+int spider_set_state(spider_ctx* c, const double* theta, int64_t step) {
+  if (!c || !theta || step < 0) return SPIDER_E_INVAL;
+  const size_t M = c->v.M;
+  std::vector<float4> buf(M);
+  for (size_t m = 0; m < M; ++m) {
+    const double* x = theta + 4 * (size_t)c->ev_old[m];
+    const double* t = &c->th0[4 * m];
+    for (int a = 0; a < 4; ++a)
+      if (!std::isfinite(x[a])) {
+        c->err = "non-finite state";
+        return SPIDER_E_INVAL;
+      }
+    buf[m] = make_float4((float)(x[0] - t[0]), (float)(x[1] - t[1]), (float)(x[2] - t[2]), (float)(x[3] - t[3]));
+  }
+  CK(c, cudaMemcpyAsync(c->v.dth, buf.data(), M * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+  c->cur = 0;
+  CK(c, launch_cen_init(c->v, 0, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->step = step;
+  return SPIDER_OK;
+}
+
+int spider_sync(spider_ctx* c) {
+  if (!c) return SPIDER_E_INVAL;
+  CK(c, cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+int spider_set_timing(spider_ctx* c, int enable) {
+  if (!c) return SPIDER_E_INVAL;
+  c->timing = enable != 0;
+  return SPIDER_OK;
+}
+
+int spider_last_timing(spider_ctx* c, float out_ms[5], int64_t* pairs, int64_t* n_obs, int32_t* pcg_iters) {
+  if (!c) return SPIDER_E_INVAL;
+  int32_t cnt[3] = {0, 0, 0};
+  CK(c, cudaMemcpyAsync(cnt, c->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (out_ms) {
+    for (int i = 0; i < 5; ++i) out_ms[i] = 0.f;
+    if (c->have_timing) {
+      for (int i = 0; i < 4; ++i) CK(c, cudaEventElapsedTime(&out_ms[i], c->ev[i], c->ev[i + 1]));
+      CK(c, cudaEventElapsedTime(&out_ms[4], c->ev[0], c->ev[4]));
+    }
+  }
+  if (pairs) *pairs = cnt[kCntPairs];
+  if (n_obs) *n_obs = cnt[kCntObs];
+  if (pcg_iters) *pcg_iters = cnt[kCntIters];
+  return SPIDER_OK;
+}
+
+int spider_debug_blocks(spider_ctx* c, int64_t* out, int64_t cap, int64_t* n) {
+  if (!c || !n || (cap > 0 && !out)) return SPIDER_E_INVAL;
+  std::vector<int32_t> s(c->last_nb);
+  if (c->last_nb)
+    CK(c, cudaMemcpyAsync(s.data(), c->v.sel, c->last_nb * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int64_t k = std::min<int64_t>(cap, c->last_nb);
+  for (int64_t i = 0; i < k; ++i) out[i] = s[i];
+  *n = c->last_nb;
+  return SPIDER_OK;
+}
+
+int spider_debug_obs(spider_ctx* c, int64_t* idx_out, float* r_out, float* q_out, int64_t cap, int64_t* n) {
+  if (!c || !n) return SPIDER_E_INVAL;
+  std::vector<int32_t> s(c->last_nb);
+  if (c->last_nb)
+    CK(c, cudaMemcpyAsync(s.data(), c->v.sel, c->last_nb * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int64_t B = c->v.B, N = c->v.N;
+  int64_t w = 0;
+  std::vector<float> rb(B), qb(B);
+  for (int64_t i = 0; i < c->last_nb; ++i) {
+    const int64_t e0 = (int64_t)s[i] * B, ne = std::min(B, N - e0);
+    if (w + ne <= cap) {
+      CK(c, cudaMemcpy(rb.data(), c->v.r_obs + e0, ne * sizeof(float), cudaMemcpyDeviceToHost));
+      CK(c, cudaMemcpy(qb.data(), c->v.q_obs + e0, ne * sizeof(float), cudaMemcpyDeviceToHost));
+      for (int64_t e = 0; e < ne; ++e) {
+        if (idx_out) idx_out[w + e] = c->ord[e0 + e];
+        if (r_out) r_out[w + e] = rb[e];
+        if (q_out) q_out[w + e] = qb[e];
+      }
+    }
+    w += ne;
+  }
+  *n = w;
+  return SPIDER_OK;
+}
+
+const char* spider_last_error(const spider_ctx* c) { return c ? c->err.c_str() : g_static_err; }
+
+void spider_destroy(spider_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  free_all(c->allocs);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int spider_net_upload(const spider_net* net, int32_t precision, spider_netdev** out) {
+  if (!out) return SPIDER_E_INVAL;
+  *out = nullptr;
+  std::string msg;
+  int rc = check_net(net, precision, &msg);
+  if (rc) {
+    static thread_local std::string last;
+    last = msg;
+    g_static_err = last.c_str();
+    return rc;
+  }
+  spider_netdev* nd = new spider_netdev();
+  cudaError_t e = upload_net(net, precision, &nd->net, nd->allocs, 0);
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nd->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t scr = e == cudaSuccess ? tt_scratch_floats(nd->net, nd->num_sms) : 0;
+  if (e == cudaSuccess && scr) e = dalloc(nd->allocs, &nd->scratch, scr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    g_static_err = cudaGetErrorString(e);
+    free_all(nd->allocs);
+    delete nd;
+    return e == cudaErrorMemoryAllocation ? SPIDER_E_OOM : SPIDER_E_CUDA;
+  }
+  *out = nd;
+  return SPIDER_OK;
+}
+
+void spider_net_free(spider_netdev* nd) {
+  if (!nd) return;
+  cudaDeviceSynchronize();
+  free_all(nd->allocs);
+  delete nd;
+}
+
+int spider_tt_pairs(const spider_netdev* nd, int64_t P, const float* src, const float* rcv, float* T_hi,
+                    float* T_lo, float* J, void* stream) {
+  if (!nd || P < 0 || (P > 0 && (!src || !rcv || !T_hi))) return SPIDER_E_INVAL;
+  if (P == 0) return SPIDER_OK;
+  if (P > (int64_t)INT32_MAX) return SPIDER_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // T is produced as (hi, lo) pairs; split into the caller's arrays afterwards
+  float2* T2 = nullptr;
+  cudaError_t e = cudaMallocAsync(&T2, (size_t)P * sizeof(float2), st);
+  if (e != cudaSuccess) { g_static_err = cudaGetErrorString(e); return SPIDER_E_OOM; }
+  PairSource ps{};
+  ps.src = reinterpret_cast<const float4*>(src);
+  ps.rcv = reinterpret_cast<const float4*>(rcv);
+  ps.n_host = P;
+  TTOut o{T2, reinterpret_cast<float4*>(J)};
+  e = launch_tt(nd->net, ps, o, nd->num_sms, nd->scratch, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(T_hi, sizeof(float), T2, sizeof(float2), sizeof(float), (size_t)P,
+                          cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && T_lo)
+    e = cudaMemcpy2DAsync(T_lo, sizeof(float), reinterpret_cast<float*>(T2) + 1, sizeof(float2), sizeof(float),
+                          (size_t)P, cudaMemcpyDeviceToDevice, st);
+  cudaError_t e2 = cudaFreeAsync(T2, st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    g_static_err = cudaGetErrorString(e);
+    return SPIDER_E_CUDA;
+  }
+  return SPIDER_OK;
+}
+
+int spider_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int64_t n,
+                        uint32_t* out) {
+  if (n < 0 || (n > 0 && !out) || n > (int64_t(1) << 28)) return SPIDER_E_INVAL;
+  if (n == 0) return SPIDER_OK;
+  uint32_t* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, (size_t)n * 16);
+  if (e != cudaSuccess) { g_static_err = cudaGetErrorString(e); return SPIDER_E_OOM; }
+  e = launch_philox_words(seed, c0, c1, c2, c3, n, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)n * 16, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    g_static_err = cudaGetErrorString(e);
+    return SPIDER_E_CUDA;
+  }
+  return SPIDER_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,681 @@
+// Step kernels: minibatch selection, the minibatch pair table, residuals,
+// whitening (Eq. marginal_sigma through the push-through identity, solved by
+// Jacobi-preconditioned CG in one cooperative launch), the deterministic
+// scatter of dlogp/dT onto pairs and events, and the fused prior + SGLD update.
+//
+// Determinism: every reduction runs in a fixed order (per-node half-edge lists
+// in observation order, per-pair occurrence lists in block order, per-CTA
+// partials summed by index); no floating-point atomics anywhere.
+#include <cuda_runtime.h>
+
+#include "dfloat.cuh"
+#include "kernels.h"
+#include "philox.cuh"
+#include "spider.h"
+
+namespace spider {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void set_error(int32_t* counters, int code) {
+  atomicCAS(&counters[kCntError], 0, code);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum with a fixed reduction tree (deterministic). All threads get it.
+template <typename T>
+__device__ T block_sum(T v, T* sm /* >= 32 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  T t = lane < nw ? sm[lane] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sm[0] = t;
+  __syncthreads();
+  T r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+// Exclusive block scan of small integers; returns the prefix, *total = sum.
+__device__ int block_exscan(int v, int* sm /* >= 33 */, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) sm[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < nw ? sm[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) sm[lane] = s;  // inclusive per-warp totals
+  }
+  __syncthreads();
+  int warp_base = wid ? sm[wid - 1] : 0;
+  *total = sm[nw - 1];
+  __syncthreads();
+  return warp_base + x - v;
+}
+
+// Sum over the selected occurrences of pair p of vals[q] (block order).
+__device__ __forceinline__ float merge_occ(const StepView& v, int32_t p, int tag, const float* vals) {
+  float a = 0.f;
+  for (int32_t t = v.inc_off[p], t1 = v.inc_off[p + 1]; t < t1; ++t)
+    if (v.blk_stamp[v.inc_b[t]] == tag) a += vals[v.inc_q[t]];
+  return a;
+}
+
+// ------------------------------------------------------------------ selection
+__global__ void k_select(StepView v, int64_t n_b, int full, uint64_t seed, int tag) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_b) return;
+  int64_t b = full ? s : feistel_index(s, v.NB, seed);
+  if (b < 0 || b >= v.NB) {
+    set_error(v.counters, SPIDER_E_TIMEOUT);
+    b = s % v.NB;
+  }
+  v.sel[s] = (int32_t)b;
+  v.blk_stamp[b] = tag;
+  int64_t sz = (b == v.NB - 1) ? (v.N - (v.NB - 1) * v.B) : v.B;
+  atomicAdd(&v.counters[kCntObs], (int)sz);
+}
+
+// owner of each local node = its occurrence in the selected block of lowest id
+__global__ void k_owner(StepView v, int tag) {
+  __shared__ int sm[33];
+  const int s = blockIdx.x;
+  const int32_t b = v.sel[s];
+  const int32_t q0 = v.blk_node_off[b], q1 = v.blk_node_off[b + 1];
+  int cnt = 0;
+  for (int32_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int32_t p = v.node_pair[q];
+    int32_t qo = -1;
+    int c = 0;
+    for (int32_t t = v.inc_off[p], t1 = v.inc_off[p + 1]; t < t1; ++t)
+      if (v.blk_stamp[v.inc_b[t]] == tag) {
+        if (qo < 0) qo = v.inc_q[t];
+        ++c;
+      }
+    v.owner_q[q] = qo;
+    v.multi[q] = (uint8_t)(c > 1);
+    cnt += (qo == q);
+  }
+  int tot = block_sum<int>(cnt, sm);
+  if (threadIdx.x == 0) v.blk_owner_cnt[s] = tot;
+}
+
+__global__ void k_scan_owner(StepView v, int64_t n_b) {
+  __shared__ int sm[33];
+  int carry = 0;
+  for (int64_t c = 0; c < n_b; c += blockDim.x) {
+    int64_t s = c + threadIdx.x;
+    int val = s < n_b ? v.blk_owner_cnt[s] : 0;
+    int total;
+    int pre = block_exscan(val, sm, &total);
+    if (s < n_b) v.blk_owner_off[s] = carry + pre;
+    carry += total;
+  }
+  if (threadIdx.x == 0) v.counters[kCntPairs] = carry;
+}
+
+__global__ void k_assign(StepView v) {
+  __shared__ int sm[33];
+  const int s = blockIdx.x;
+  const int32_t b = v.sel[s];
+  const int32_t q0 = v.blk_node_off[b], q1 = v.blk_node_off[b + 1];
+  int carry = v.blk_owner_off[s];
+  for (int32_t c = q0; c < q1; c += blockDim.x) {
+    int32_t q = c + threadIdx.x;
+    int own = (q < q1) && (v.owner_q[q] == q);
+    int total;
+    int pre = block_exscan(own, sm, &total);
+    if (own) {
+      int u = carry + pre;
+      v.loc2u[q] = u;
+      v.uniq_pair[u] = v.node_pair[q];
+      v.uniq_q[u] = q;
+    }
+    carry += total;
+  }
+}
+
+__global__ void k_link(StepView v) {
+  const int32_t b = v.sel[blockIdx.x];
+  const int32_t q0 = v.blk_node_off[b], q1 = v.blk_node_off[b + 1];
+  for (int32_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    int32_t qo = v.owner_q[q];
+    if (qo != q) v.loc2u[q] = v.loc2u[qo];
+  }
+}
+
+// ------------------------------------------------------------------ residuals
+// r_n = dt~_n - [(T_i - T_j) + (dt0_i - dt0_j)]  (Eq. 1; dt~ = dt - (t0_i - t0_j) of theta_0)
+// and the whitening right-hand side u = B^T r, diag(B^T B) per node.
+__global__ void k_resid(StepView v) {
+  extern __shared__ float smf[];
+  __shared__ double smd[33];
+  const int L_max = v.L_max;
+  float* Thi = smf;
+  float* Tlo = Thi + L_max;
+  float* t0 = Tlo + L_max;
+  float* rs = t0 + L_max;
+  float* sw = rs + v.B;
+  const int s = blockIdx.x;
+  const int32_t b = v.sel[s];
+  const int32_t q0 = v.blk_node_off[b];
+  const int L = v.blk_node_off[b + 1] - q0;
+  const int64_t e0 = (int64_t)b * v.B;
+  const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const int32_t q = q0 + l;
+    const float2 t = v.T2[v.loc2u[q]];
+    Thi[l] = t.x;
+    Tlo[l] = t.y;
+    t0[l] = v.dth[v.pair_ev[v.node_pair[q]]].w;
+  }
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) sw[e] = v.obs_sw[e0 + e];
+  __syncthreads();
+  double rr = 0.0;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const uint32_t lij = v.obs_l[e0 + e];
+    const int li = lij & 0xFFFF, lj = lij >> 16;
+    const float dhi = Thi[li] - Thi[lj];
+    const float dlo = Tlo[li] - Tlo[lj];
+    const float dt0 = t0[li] - t0[lj];
+    const float r = ((v.obs_dt[e0 + e] - dhi) - dt0) - dlo;
+    rs[e] = r;
+    v.r_obs[e0 + e] = r;
+    rr += (double)r * (double)r;
+  }
+  rr = block_sum<double>(rr, smd);
+  if (threadIdx.x == 0) v.dblk[s] = rr;
+  __syncthreads();
+  if (!v.whiten) return;
+  const uint16_t* he = v.blk_he + 2 * e0;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const int32_t q = q0 + l;
+    const int h0 = v.node_he[q];
+    const int h1 = (l + 1 < L) ? (int)v.node_he[q + 1] : 2 * ne;
+    float a = 0.f, d = 0.f;
+    for (int h = h0; h < h1; ++h) {
+      const int code = he[h];
+      const int e = code >> 1;
+      const float w = sw[e];
+      a += (code & 1) ? -w * rs[e] : w * rs[e];
+      d += w * w;
+    }
+    if (!v.multi[q]) {
+      const int32_t u = v.loc2u[q];
+      v.rhs[u] = a;
+      v.diag[u] = v.lam + d;
+    } else {
+      v.part_a[q] = a;
+      v.part_b[q] = d;
+    }
+  }
+}
+
+__global__ void k_merge_rhs(StepView v, int tag) {
+  const int32_t P_u = v.counters[kCntPairs];
+  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
+    const int32_t q = v.uniq_q[u];
+    if (!v.multi[q]) continue;
+    const int32_t p = v.node_pair[q];
+    v.rhs[u] = merge_occ(v, p, tag, v.part_a);
+    v.diag[u] = v.lam + merge_occ(v, p, tag, v.part_b);
+  }
+}
+
+// ------------------------------------------------------------------ whitening
+// Software grid barrier for a cooperative launch, with a bounded wait
+// (globaltimer, 2 s): on timeout the error flag is set and the caller returns.
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_barrier(int32_t* counters) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    volatile int32_t* gen = counters + kCntBarGen;
+    const int32_t g0 = *gen;
+    __threadfence();
+    const int32_t arrived = atomicAdd(&counters[kCntBarArrive], 1);
+    ok = 1;
+    if (arrived == (int)gridDim.x - 1) {
+      counters[kCntBarArrive] = 0;
+      __threadfence();
+      atomicAdd(&counters[kCntBarGen], 1);
+    } else {
+      const uint64_t t0 = gtimer();
+      while (*gen == g0) {
+        if (((volatile int32_t*)counters)[kCntError] != 0) { ok = 0; break; }
+        if (gtimer() - t0 > 2000000000ull) {
+          set_error(counters, SPIDER_E_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Fixed-order sum of G partials (every CTA computes the same value).
+__device__ float sum_partials(const float* part, int G, float* sm) {
+  float a = 0.f;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) a += part[i];
+  return block_sum<float>(a, sm);
+}
+
+// Solve (lambda I + B^T B) z = u with Jacobi-preconditioned CG over all
+// station groups at once (the nodes of different groups never share an edge).
+__global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n_b, int max_it, float tol) {
+  extern __shared__ float pl[];
+  __shared__ float smr[33];
+  const int G = gridDim.x;
+  const int32_t P_u = v.counters[kCntPairs];
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = G * blockDim.x;
+  float* red = v.red;
+  // z = 0, r = u, y = D^-1 r, p = y
+  float rz = 0.f, bb = 0.f;
+  for (int32_t u = gtid; u < P_u; u += gstride) {
+    const float r = v.rhs[u];
+    const float y = r / v.diag[u];
+    v.z[u] = 0.f;
+    v.res[u] = r;
+    v.pv[u] = y;
+    rz += r * y;
+    bb += r * r;
+  }
+  rz = block_sum<float>(rz, smr);
+  bb = block_sum<float>(bb, smr);
+  if (threadIdx.x == 0) {
+    red[0 * kMaxGrid + blockIdx.x] = rz;
+    red[1 * kMaxGrid + blockIdx.x] = bb;
+  }
+  if (!grid_barrier(v.counters)) return;
+  rz = sum_partials(red + 0 * kMaxGrid, G, smr);
+  bb = sum_partials(red + 1 * kMaxGrid, G, smr);
+  int it = 0;
+  const float thr = tol * tol * bb;
+  if (bb > 0.f) {
+    for (it = 0; it < max_it;) {
+      // Ap = lambda p + B^T B p : per selected block, node sums over its half-edges
+      for (int64_t s = blockIdx.x; s < n_b; s += G) {
+        const int32_t b = v.sel[s];
+        const int32_t q0 = v.blk_node_off[b];
+        const int L = v.blk_node_off[b + 1] - q0;
+        const int64_t e0 = (int64_t)b * v.B;
+        const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
+        __syncthreads();
+        for (int l = threadIdx.x; l < L; l += blockDim.x) pl[l] = v.pv[v.loc2u[q0 + l]];
+        __syncthreads();
+        const uint16_t* he = v.blk_he + 2 * e0;
+        for (int l = threadIdx.x; l < L; l += blockDim.x) {
+          const int32_t q = q0 + l;
+          const int h0 = v.node_he[q];
+          const int h1 = (l + 1 < L) ? (int)v.node_he[q + 1] : 2 * ne;
+          const float pself = pl[l];
+          float acc = 0.f;
+          for (int h = h0; h < h1; ++h) {
+            const int code = he[h];
+            const int e = code >> 1;
+            const uint32_t lij = v.obs_l[e0 + e];
+            const int other = (code & 1) ? (int)(lij & 0xFFFF) : (int)(lij >> 16);
+            const float w = v.obs_sw[e0 + e];
+            acc += (w * w) * (pself - pl[other]);
+          }
+          if (!v.multi[q]) v.Ap[v.loc2u[q]] = v.lam * pself + acc;
+          else v.part_a[q] = acc;
+        }
+      }
+      if (!grid_barrier(v.counters)) return;
+      float pap = 0.f;
+      for (int32_t u = gtid; u < P_u; u += gstride) {
+        const int32_t q = v.uniq_q[u];
+        float ap;
+        if (v.multi[q]) {
+          ap = v.lam * v.pv[u] + merge_occ(v, v.node_pair[q], tag, v.part_a);
+          v.Ap[u] = ap;
+        } else {
+          ap = v.Ap[u];
+        }
+        pap += v.pv[u] * ap;
+      }
+      pap = block_sum<float>(pap, smr);
+      if (threadIdx.x == 0) red[2 * kMaxGrid + blockIdx.x] = pap;
+      if (!grid_barrier(v.counters)) return;
+      pap = sum_partials(red + 2 * kMaxGrid, G, smr);
+      const float alpha = rz / pap;
+      float rzn = 0.f, rr = 0.f;
+      for (int32_t u = gtid; u < P_u; u += gstride) {
+        v.z[u] += alpha * v.pv[u];
+        const float r = v.res[u] - alpha * v.Ap[u];
+        v.res[u] = r;
+        const float y = r / v.diag[u];
+        v.yv[u] = y;
+        rzn += r * y;
+        rr += r * r;
+      }
+      rzn = block_sum<float>(rzn, smr);
+      rr = block_sum<float>(rr, smr);
+      if (threadIdx.x == 0) {
+        red[3 * kMaxGrid + blockIdx.x] = rzn;
+        red[4 * kMaxGrid + blockIdx.x] = rr;
+      }
+      if (!grid_barrier(v.counters)) return;
+      rzn = sum_partials(red + 3 * kMaxGrid, G, smr);
+      rr = sum_partials(red + 4 * kMaxGrid, G, smr);
+      ++it;
+      if (rr <= thr || !(pap > 0.f)) break;
+      const float beta = rzn / rz;
+      rz = rzn;
+      for (int32_t u = gtid; u < P_u; u += gstride) v.pv[u] = v.yv[u] + beta * v.pv[u];
+      if (!grid_barrier(v.counters)) return;
+    }
+  } else {
+    for (int32_t u = gtid; u < P_u; u += gstride) v.z[u] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) v.counters[kCntIters] = it;
+}
+
+// q_e = sigma^-2 (r_e - sqrt(w_e) (z_i - z_j)) and the node sums
+// s_p = sum_{e: p = i-end} q_e - sum_{e: p = j-end} q_e  (= d loglik / d T_p)
+__global__ void k_final(StepView v) {
+  extern __shared__ float smf[];
+  float* zl = smf;
+  float* qs = zl + v.L_max;
+  const int s = blockIdx.x;
+  const int32_t b = v.sel[s];
+  const int32_t q0 = v.blk_node_off[b];
+  const int L = v.blk_node_off[b + 1] - q0;
+  const int64_t e0 = (int64_t)b * v.B;
+  const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
+  for (int l = threadIdx.x; l < L; l += blockDim.x) zl[l] = v.whiten ? v.z[v.loc2u[q0 + l]] : 0.f;
+  __syncthreads();
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const uint32_t lij = v.obs_l[e0 + e];
+    const float bz = v.obs_sw[e0 + e] * (zl[lij & 0xFFFF] - zl[lij >> 16]);
+    const float qe = v.inv_s2 * (v.r_obs[e0 + e] - bz);
+    qs[e] = qe;
+    v.q_obs[e0 + e] = qe;
+  }
+  __syncthreads();
+  const uint16_t* he = v.blk_he + 2 * e0;
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const int32_t q = q0 + l;
+    const int h0 = v.node_he[q];
+    const int h1 = (l + 1 < L) ? (int)v.node_he[q + 1] : 2 * ne;
+    float a = 0.f;
+    for (int h = h0; h < h1; ++h) {
+      const int code = he[h];
+      a += (code & 1) ? -qs[code >> 1] : qs[code >> 1];
+    }
+    if (!v.multi[q]) v.s_u[v.loc2u[q]] = a;
+    else v.part_a[q] = a;
+  }
+}
+
+// s_p * (N/n) times (dT/dx_p, 1) into the global pair slots, stamped.
+__global__ void k_merge_s(StepView v, int tag) {
+  __shared__ double smd[33];
+  const int32_t P_u = v.counters[kCntPairs];
+  const float scale = (float)((double)v.N / (double)v.counters[kCntObs]);
+  double uz = 0.0;
+  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
+    const int32_t q = v.uniq_q[u];
+    const int32_t p = v.node_pair[q];
+    float sp = v.multi[q] ? merge_occ(v, p, tag, v.part_a) : v.s_u[u];
+    sp *= scale;
+    const float4 J = v.J[u];
+    v.gp[p] = make_float4(sp * J.x, sp * J.y, sp * J.z, sp);
+    v.pstamp[p] = tag;
+    v.estamp[v.pair_ev[p]] = tag;
+    if (v.whiten) uz += (double)v.rhs[u] * (double)v.z[u];
+  }
+  uz = block_sum<double>(uz, smd);
+  if (threadIdx.x == 0) v.dred[kMaxGrid + blockIdx.x] = uz;   // slot 1
+}
+
+// ------------------------------------------------------------------ events
+// grad_m = (N/n) sum_k s_(m,k) (dT/dx, 1) - dtheta_m / sigma_e^2
+//          - mean(dtheta) / (M sigma_c^2)             (priors of Sec. 3.1)
+// mode 0: write grad; mode 1: SGLD theta += eps grad + ns sqrt(2 eps) eta (Sec. 3.2)
+__global__ void k_event(StepView v, int tag, int mode, float eps, float noise_scale, uint64_t seed,
+                        int cur, int64_t sample_slot) {
+  __shared__ float4 scen;
+  __shared__ float smr[33];
+  __shared__ double smd[33];
+  const int G = v.cen_grid;
+  // centroid of the current state from the fixed partials of the previous pass
+  if (threadIdx.x < 32) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < G; i += 32) {
+      const float4 c = v.cen_part[cur * kMaxGrid + i];
+      a.x += c.x; a.y += c.y; a.z += c.z; a.w += c.w;
+    }
+    a.x = warp_sum(a.x); a.y = warp_sum(a.y); a.z = warp_sum(a.z); a.w = warp_sum(a.w);
+    if (threadIdx.x == 0) {
+      const float invM = 1.0f / (float)v.M;
+      scen = make_float4(a.x * invM, a.y * invM, a.z * invM, a.w * invM);
+    }
+  }
+  __syncthreads();
+  const float4 cen = scen;
+  const float4 ise = v.inv_sig_e2, isc = v.inv_sig_c2;
+  const float invM = 1.0f / (float)v.M;
+  const float4 gc = make_float4(cen.x * isc.x * invM, cen.y * isc.y * invM, cen.z * isc.z * invM,
+                                cen.w * isc.w * invM);
+  const float sq = noise_scale * sqrtf(2.0f * eps);
+  const uint2 key = seed_key(seed);
+  float4 csum = make_float4(0.f, 0.f, 0.f, 0.f);
+  double lp = 0.0;
+  int bad = 0;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M; m += (int64_t)G * blockDim.x) {
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v.estamp[m] == tag) {
+      for (int32_t p = v.pair_off[m], p1 = v.pair_off[m + 1]; p < p1; ++p)
+        if (v.pstamp[p] == tag) {
+          const float4 c = v.gp[p];
+          g.x += c.x; g.y += c.y; g.z += c.z; g.w += c.w;
+        }
+    }
+    const float4 d = v.dth[m];
+    g.x -= d.x * ise.x + gc.x;
+    g.y -= d.y * ise.y + gc.y;
+    g.z -= d.z * ise.z + gc.z;
+    g.w -= d.w * ise.w + gc.w;
+    if (mode == 0) {
+      v.grad[m] = g;
+      lp += (double)d.x * d.x * ise.x + (double)d.y * d.y * ise.y + (double)d.z * d.z * ise.z +
+            (double)d.w * d.w * ise.w;
+      if (!(isfinite(g.x) && isfinite(g.y) && isfinite(g.z) && isfinite(g.w))) bad = 1;
+      csum.x += d.x; csum.y += d.y; csum.z += d.z; csum.w += d.w;
+    } else {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)m, v.chain, v.catalog, kTagNoise), key);
+      const float2 n01 = box_muller(w.x, w.y), n23 = box_muller(w.z, w.w);
+      float4 nd;
+      nd.x = d.x + eps * g.x + sq * n01.x;
+      nd.y = d.y + eps * g.y + sq * n01.y;
+      nd.z = d.z + eps * g.z + sq * n23.x;
+      nd.w = d.w + eps * g.w + sq * n23.y;
+      if (!(isfinite(nd.x) && isfinite(nd.y) && isfinite(nd.z) && isfinite(nd.w))) bad = 1;
+      v.dth[m] = nd;
+      if (sample_slot >= 0) v.samples[sample_slot * v.M + m] = nd;
+      csum.x += nd.x; csum.y += nd.y; csum.z += nd.z; csum.w += nd.w;
+    }
+  }
+  if (bad) set_error(v.counters, SPIDER_E_NONFINITE);
+  csum.x = block_sum<float>(csum.x, smr);
+  csum.y = block_sum<float>(csum.y, smr);
+  csum.z = block_sum<float>(csum.z, smr);
+  csum.w = block_sum<float>(csum.w, smr);
+  if (mode == 1 && threadIdx.x == 0) v.cen_part[(cur ^ 1) * kMaxGrid + blockIdx.x] = csum;
+  if (mode == 0) {
+    lp = block_sum<double>(lp, smd);
+    if (threadIdx.x == 0) v.dred[2 * kMaxGrid + blockIdx.x] = lp;   // slot 2
+  }
+}
+
+// centroid partials of the current state (after create / set_state)
+__global__ void k_cen_init(StepView v, int cur) {
+  __shared__ float smr[33];
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M;
+       m += (int64_t)v.cen_grid * blockDim.x) {
+    const float4 d = v.dth[m];
+    c.x += d.x; c.y += d.y; c.z += d.z; c.w += d.w;
+  }
+  c.x = block_sum<float>(c.x, smr);
+  c.y = block_sum<float>(c.y, smr);
+  c.z = block_sum<float>(c.z, smr);
+  c.w = block_sum<float>(c.w, smr);
+  if (threadIdx.x == 0) v.cen_part[cur * kMaxGrid + blockIdx.x] = c;
+}
+
+// FP64 log posterior: -1/2 (N/n) sigma^-2 (r.r - u.z) - 1/2 |dtheta/sigma_e|^2
+//                     - 1/2 |mean(dtheta)/sigma_c|^2   (constants dropped)
+__global__ void k_logpost(StepView v, int64_t n_b, int gu, int cur) {
+  __shared__ double smd[33];
+  double rr = 0.0, uz = 0.0, lp = 0.0;
+  for (int64_t i = threadIdx.x; i < n_b; i += blockDim.x) rr += v.dblk[i];
+  for (int i = threadIdx.x; i < gu; i += blockDim.x) uz += v.dred[kMaxGrid + i];
+  for (int i = threadIdx.x; i < v.cen_grid; i += blockDim.x) lp += v.dred[2 * kMaxGrid + i];
+  rr = block_sum<double>(rr, smd);
+  uz = block_sum<double>(uz, smd);
+  lp = block_sum<double>(lp, smd);
+  double c[4] = {0, 0, 0, 0};
+  for (int i = 0; i < v.cen_grid; ++i) {
+    const float4 p = v.cen_part[cur * kMaxGrid + i];
+    c[0] += p.x; c[1] += p.y; c[2] += p.z; c[3] += p.w;
+  }
+  if (threadIdx.x == 0) {
+    const double scale = (double)v.N / (double)v.counters[kCntObs];
+    const double quad = (double)v.inv_s2 * (rr - (v.whiten ? uz : 0.0));
+    const double ll = -0.5 * scale * quad;
+    const double lpr = -0.5 * lp;
+    const float isc[4] = {v.inv_sig_c2.x, v.inv_sig_c2.y, v.inv_sig_c2.z, v.inv_sig_c2.w};
+    double lc = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      const double mu = c[a] / (double)v.M;
+      lc += mu * mu * (double)isc[a];
+    }
+    lc *= -0.5;
+    v.dout[0] = ll;
+    v.dout[1] = lpr;
+    v.dout[2] = lc;
+    v.dout[3] = ll + lpr + lc;
+  }
+}
+
+__global__ void k_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                               int64_t n, uint32_t* out) {
+  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  uint4 w = philox4x32_10(make_uint4(c0 + (uint32_t)m, c1, c2, c3), seed_key(seed));
+  reinterpret_cast<uint4*>(out)[m] = w;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+static inline int grid_for(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+cudaError_t launch_select(const StepView& v, int64_t n_b, int full, uint64_t seed, int tag, cudaStream_t st) {
+  k_select<<<grid_for(n_b), kThreads, 0, st>>>(v, n_b, full, seed, tag);
+  k_owner<<<(unsigned)n_b, kThreads, 0, st>>>(v, tag);
+  k_scan_owner<<<1, 1024, 0, st>>>(v, n_b);
+  k_assign<<<(unsigned)n_b, kThreads, 0, st>>>(v);
+  k_link<<<(unsigned)n_b, kThreads, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+size_t resid_smem(const StepView& v) { return (size_t)(3 * v.L_max + 2 * v.B) * sizeof(float); }
+size_t final_smem(const StepView& v) { return (size_t)(v.L_max + v.B) * sizeof(float); }
+size_t pcg_smem(const StepView& v) { return (size_t)v.L_max * sizeof(float); }
+
+cudaError_t configure_step_kernels(const StepView& v) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)resid_smem(v))))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)final_smem(v))))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcg_smem(v))))
+    return e;
+  return cudaSuccess;
+}
+
+int pcg_grid(const StepView& v, int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kThreads, pcg_smem(v)) != cudaSuccess ||
+      per_sm < 1)
+    return 0;
+  int g = num_sms * per_sm;
+  return g > kMaxGrid ? kMaxGrid : g;
+}
+
+cudaError_t launch_resid(const StepView& v, int64_t n_b, int tag, int gu, cudaStream_t st) {
+  k_resid<<<(unsigned)n_b, kThreads, resid_smem(v), st>>>(v);
+  if (v.whiten) k_merge_rhs<<<gu, kThreads, 0, st>>>(v, tag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg(const StepView& v, int tag, int64_t n_b, int max_it, float tol, int grid,
+                       cudaStream_t st) {
+  if (!v.whiten) return cudaSuccess;
+  StepView vv = v;
+  int tg = tag;
+  int64_t nb = n_b;
+  int mi = max_it;
+  float tl = tol;
+  void* args[] = {&vv, &tg, &nb, &mi, &tl};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(kThreads), args,
+                                     pcg_smem(v), st);
+}
+
+cudaError_t launch_finish(const StepView& v, int64_t n_b, int tag, int gu, int mode, float eps,
+                          float noise_scale, uint64_t seed, int cur, int64_t sample_slot,
+                          cudaStream_t st) {
+  k_final<<<(unsigned)n_b, kThreads, final_smem(v), st>>>(v);
+  k_merge_s<<<gu, kThreads, 0, st>>>(v, tag);
+  k_event<<<v.cen_grid, kThreads, 0, st>>>(v, tag, mode, eps, noise_scale, seed, cur, sample_slot);
+  if (mode == 0) k_logpost<<<1, kThreads, 0, st>>>(v, n_b, gu, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cen_init(const StepView& v, int cur, cudaStream_t st) {
+  k_cen_init<<<v.cen_grid, kThreads, 0, st>>>(v, cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                int64_t n, uint32_t* out, cudaStream_t st) {
+  k_philox_words<<<grid_for(n), kThreads, 0, st>>>(seed, c0, c1, c2, c3, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace spider

@@ -1,0 +1,130 @@
+// Device-side views shared by the step kernels (plain pointers, passed by value).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spider {
+
+// counters[] slots (int32, device)
+enum : int {
+  kCntPairs = 0,     // P_u: unique pairs of the current minibatch
+  kCntObs = 1,       // n: observations of the current minibatch
+  kCntIters = 2,     // whitening iterations used
+  kCntError = 3,     // first device-side error (SPIDER_E_*), sticky until read
+  kCntBarArrive = 4, // grid barrier arrivals
+  kCntBarGen = 5,    // grid barrier generation
+  kCntSlots = 8
+};
+
+// Travel-time network on the device.
+struct NetView {
+  int kind;          // SPIDER_TT_*
+  int H;
+  int precision;     // SPIDER_FP32 / BF16 / FP8
+  float v0, g;
+  float inv_v_hi, inv_v_lo;   // 1/v0 as a double-float
+  const float* W1;   // H x 6 (out, in)
+  const float* b1;   // H
+  const float* Wt[3];  // W2..W4 transposed: [in][out] (forward operand)
+  const float* Wn[3];  // W2..W4 as given: [out][in] (backward operand)
+  const float* bh[3];  // b2..b4
+  const float* W5;     // H
+  float b5;
+  const void* tc;      // tensor-core operand images (BF16 / FP8), null in FP32
+  const float* tc_scale;  // per-layer FP8 dequantisation scales (6), null otherwise
+};
+
+// Where the pairs of a travel-time launch come from.
+struct PairSource {
+  // problem mode: pair u -> uniq_pair[u] -> (event, station)
+  const int32_t* uniq_pair;
+  const int32_t* pair_ev;
+  const int32_t* pair_st;
+  const float4* th0_hi;   // event theta_0 (hi)
+  const float4* th0_lo;   // event theta_0 (lo)
+  const float4* dth;      // event state offset theta - theta_0
+  const float4* sta_hi;
+  const float4* sta_lo;
+  // raw mode (uniq_pair == nullptr): absolute FP32 positions per pair
+  const float4* src;
+  const float4* rcv;
+  const int32_t* n_dev;   // device count (problem mode) or nullptr
+  int64_t n_host;         // host count (raw mode) / upper bound
+};
+
+struct TTOut {
+  float2* T2;   // (T_hi, T_lo)
+  float4* J;    // (dT/dx, dT/dy, dT/dz, 0), may be null
+};
+
+// Step state and tables.
+struct StepView {
+  int64_t M, N, S, NB, B, P, Q;
+  int L_max;
+  const float4* th0_hi;
+  const float4* th0_lo;
+  float4* dth;
+  const float4* sta_hi;
+  const float4* sta_lo;
+  const int32_t* pair_ev;
+  const int32_t* pair_st;
+  const int32_t* pair_off;
+  const uint32_t* obs_l;
+  const float* obs_dt;
+  const float* obs_sw;
+  const int32_t* blk_node_off;
+  const int32_t* node_pair;
+  const uint16_t* node_he;
+  const uint16_t* blk_he;
+  const int32_t* inc_off;
+  const int32_t* inc_q;
+  const int32_t* inc_b;
+  // per-step scratch
+  int32_t* sel;
+  int32_t* blk_stamp;
+  int32_t* owner_q;
+  uint8_t* multi;
+  int32_t* loc2u;
+  int32_t* blk_owner_cnt;
+  int32_t* blk_owner_off;
+  int32_t* uniq_pair;
+  int32_t* uniq_q;
+  float2* T2;
+  float4* J;
+  float* r_obs;
+  float* q_obs;
+  float* part_a;
+  float* part_b;
+  float* rhs;
+  float* diag;
+  float* z;
+  float* res;
+  float* pv;
+  float* Ap;
+  float* yv;
+  float* s_u;
+  float4* gp;
+  int32_t* pstamp;
+  int32_t* estamp;
+  float4* grad;
+  int32_t* counters;
+  float* red;        // float reduction partials (whitening), 8 x kMaxGrid
+  double* dblk;      // FP64 sum r^2 per selected block (NB)
+  double* dred;      // FP64 diagnostics partials, 4 x kMaxGrid
+  double* dout;      // FP64 results: [0] loglik (scaled), [1] logprior, [2] logcen, [3] logpost
+  float4* cen_part;  // 2 x kMaxGrid centroid partial sums
+  float4* samples;
+  int64_t sample_cap;
+  // constants
+  float lam;        // sigma^2 / kappa^2
+  float inv_s2;     // 1 / sigma^2
+  int whiten;       // kappa > 0
+  float4 inv_sig_e2;   // 1 / sigma_e^2
+  float4 inv_sig_c2;   // 1 / sigma_c^2
+  int cen_grid;     // CTAs of the event kernel (fixed: centroid partials)
+  uint32_t chain, catalog;
+};
+
+constexpr int kMaxGrid = 4096;
+
+}  // namespace spider

@@ -1,0 +1,328 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (FP32 form): |dT| <= 1 us + 1/2 ulp_fp32(T); gradient rel-L2 <= 1e-5;
+bit-exact for integer work (Philox words, selected blocks, observation sets).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import spider_oracle as O
+from paper_2508_12117_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL_FP32 = 1e-5
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def t_tol(T):
+    return 1e-6 + 0.5 * np.spacing(np.abs(T).astype(np.float32)).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    torch.cuda.set_device(0)
+    return torch
+
+
+@pytest.fixture(scope="module")
+def cat1():
+    return synth.make_catalog(1)
+
+
+@pytest.fixture(scope="module")
+def cat2():
+    return synth.make_catalog(2)
+
+
+# ------------------------------------------------------------------ Philox
+@pytest.mark.parametrize("seed", [0, 1, 0xDEADBEEFCAFEF00D, 2 ** 63 + 12345])
+def test_philox_words_bit_exact(seed):
+    n = 5000
+    gpu = binding.spider_philox_words(seed, 7, 3, 5, O.TAG_NOISE, n)
+    ctr = np.stack([np.arange(7, 7 + n), np.full(n, 3), np.full(n, 5), np.full(n, O.TAG_NOISE)], 1)
+    ref = O.philox4x32_10(ctr.astype(np.uint64), np.array(O.seed_key(seed), np.uint64))
+    assert np.array_equal(gpu, ref)
+
+
+def test_philox_matches_curand_device_library(torch_cuda, tmp_path):
+    """The oracle's Philox agrees with curand's Philox4_32_10, an independent
+    implementation, run on the device from a probe compiled with nvcc here."""
+    import ctypes
+    import subprocess
+    src = tmp_path / "probe.cu"
+    src.write_text(r"""
+#include <curand_kernel.h>
+__global__ void kk(unsigned long long seed, unsigned long long sub, unsigned int* out, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  curandStatePhilox4_32_10_t s;
+  curand_init(seed, sub + t, 0, &s);
+  uint4 w = curand4(&s);
+  out[4*t+0] = w.x; out[4*t+1] = w.y; out[4*t+2] = w.z; out[4*t+3] = w.w;
+}
+extern "C" int run(unsigned long long seed, unsigned long long sub, unsigned int* out, int n) {
+  kk<<<(n + 127) / 128, 128>>>(seed, sub, out, n);
+  return (int)cudaDeviceSynchronize();
+}
+""")
+    so = tmp_path / "probe.so"
+    r = subprocess.run(["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a",
+                        "-shared", "-Xcompiler", "-fPIC", "-o", str(so), str(src)],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("could not build the curand probe: " + r.stderr[-300:])
+    lib = ctypes.CDLL(str(so))
+    torch = torch_cuda
+    n, seed, sub = 64, 0x1234_5678_9ABC, 3 << 32
+    out = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    assert lib.run(ctypes.c_ulonglong(seed), ctypes.c_ulonglong(sub), ctypes.c_void_p(out.data_ptr()),
+                   ctypes.c_int(n)) == 0
+    got = out.cpu().numpy().view(np.uint32)
+    # curand_init(seed, subsequence s, 0): counter (0, 0, lo(s), hi(s)), key = seed
+    subs = np.uint64(sub) + np.arange(n, dtype=np.uint64)
+    ctr = np.stack([np.zeros(n, np.uint64), np.zeros(n, np.uint64), subs & np.uint64(0xFFFFFFFF),
+                    subs >> np.uint64(32)], 1)
+    ref = O.philox4x32_10(ctr, np.array(O.seed_key(seed), np.uint64))
+    assert np.array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ travel times
+def _pairs(torch, n, seed=0):
+    rng = np.random.default_rng(seed)
+    src = np.c_[rng.uniform(0, 60, n), rng.uniform(0, 60, n), rng.uniform(2, 16, n)].astype(np.float32)
+    rcv = np.c_[rng.uniform(-10, 70, n), rng.uniform(-10, 70, n), np.zeros(n)].astype(np.float32)
+    return src, rcv
+
+
+def _tt_gpu(torch, nd, src, rcv):
+    P = src.shape[0]
+    s4 = torch.zeros(P, 4, device="cuda"); s4[:, :3] = torch.from_numpy(src).cuda()
+    r4 = torch.zeros(P, 4, device="cuda"); r4[:, :3] = torch.from_numpy(rcv).cuda()
+    Th = torch.empty(P, device="cuda"); Tl = torch.empty(P, device="cuda")
+    J = torch.empty(P, 4, device="cuda")
+    nd.spider_tt_pairs(P, s4.data_ptr(), r4.data_ptr(), Th.data_ptr(), Tl.data_ptr(), J.data_ptr())
+    torch.cuda.synchronize()
+    T = Th.double().cpu().numpy() + Tl.double().cpu().numpy()
+    return T, Th.cpu().numpy(), J.cpu().numpy()[:, :3]
+
+
+def test_tt_homogeneous_parity(torch_cuda):
+    torch = torch_cuda
+    src, rcv = _pairs(torch, 20000)
+    nd = binding.NetDevice(binding.Net(binding.TT_HOMOGENEOUS, v0=6.0))
+    T, Thi, J = _tt_gpu(torch, nd, src, rcv)
+    To, Jo = O.tt_homogeneous(src.astype(np.float64), rcv.astype(np.float64), 6.0)
+    assert np.all(np.abs(T - To) <= 1e-9)          # double-float: far inside 1 us
+    assert np.all(np.abs(Thi - To) <= t_tol(To))
+    assert rel_l2(J, Jo) <= 1e-6
+
+
+def test_tt_linear_gradient_parity(torch_cuda):
+    torch = torch_cuda
+    src, rcv = _pairs(torch, 20000, 1)
+    nd = binding.NetDevice(binding.Net(binding.TT_LINEAR_GRADIENT, v0=5.0, g=0.05))
+    T, Thi, J = _tt_gpu(torch, nd, src, rcv)
+    To, Jo = O.tt_linear_gradient(src.astype(np.float64), rcv.astype(np.float64), 5.0, 0.05)
+    # FP32 arccosh form: a few ulp of T
+    assert np.all(np.abs(Thi - To) <= 4 * np.spacing(To.astype(np.float32)) + 1e-6)
+    assert rel_l2(J, Jo) <= 1e-5
+
+
+@pytest.mark.parametrize("H", [128, 256])
+def test_tt_mlp_fp32_parity_and_fd(torch_cuda, H):
+    torch = torch_cuda
+    net = synth.mlp_weights(H, 1234 + H)
+    src, rcv = _pairs(torch, 4099, 2)          # 64 full tiles and a ragged tail
+    nd = binding.NetDevice(binding.Net(binding.TT_MLP, mlp=net))
+    T, Thi, J = _tt_gpu(torch, nd, src, rcv)
+    To, Jo = O.tt_mlp(src.astype(np.float64), rcv.astype(np.float64), net)
+    assert np.all(np.abs(T - To) <= t_tol(To)), np.abs(T - To).max()
+    assert rel_l2(J, Jo) <= 1e-5
+    # central differences of the GPU's own T (h = 10 m) against its Jacobian
+    h = 1e-2
+    fd = np.zeros_like(J, dtype=np.float64)
+    for a in range(3):
+        sp, sm = src.copy(), src.copy()
+        sp[:, a] += h; sm[:, a] -= h
+        Tp, _, _ = _tt_gpu(torch, nd, sp, rcv)
+        Tm, _, _ = _tt_gpu(torch, nd, sm, rcv)
+        fd[:, a] = (Tp - Tm) / ((sp[:, a].astype(np.float64) - sm[:, a]))
+    assert rel_l2(J, fd) <= 1e-3
+
+
+def test_autograd_function_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2508_12117_gb300.autograd import travel_time
+    net = synth.mlp_weights(128, 77)
+    nd = binding.NetDevice(binding.Net(binding.TT_MLP, mlp=net))
+    src, rcv = _pairs(torch, 1000, 3)
+    for mode in (False, True):          # stored Jacobian, recomputed Jacobian
+        s = torch.from_numpy(src).cuda().requires_grad_(True)
+        r = torch.from_numpy(rcv).cuda()
+        T = travel_time(s, r, nd, recompute=mode)
+        wts = torch.linspace(-1, 1, 1000, device="cuda")
+        (T * wts).sum().backward()
+        To, Jo = O.tt_mlp(src.astype(np.float64), rcv.astype(np.float64), net)
+        assert np.all(np.abs(T.detach().double().cpu().numpy() - To) <= t_tol(To) + 1e-6)
+        ref = wts.double().cpu().numpy()[:, None] * Jo
+        assert rel_l2(s.grad.double().cpu().numpy(), ref) <= 1e-5
+
+
+# ------------------------------------------------------------------ the step
+def test_tiny_full_batch_gradient_and_whitening(cat1):
+    ctx = binding.Context.from_catalog(cat1)
+    g, lp = ctx.spider_grad_logpost(0)
+    P = O.problem_from_catalog(cat1)
+    L, go, info = O.log_posterior(P, cat1.init_xyzt)
+    assert rel_l2(g, go) <= GRAD_TOL_FP32
+    assert abs(lp - L) <= 1e-6 * abs(L)
+    idx, r, q = ctx.spider_debug_obs(cat1.N + 10)
+    assert sorted(idx.tolist()) == list(range(cat1.N))
+    ro = np.empty(cat1.N); qo = np.empty(cat1.N)
+    ro[np.arange(cat1.N)] = info["r"]; qo[np.arange(cat1.N)] = info["q"]
+    assert np.abs(r - ro[idx]).max() <= 1e-6          # residuals within 1 us
+    assert rel_l2(q, qo[idx]) <= 1e-5                  # whitened residuals Sigma^-1 r
+    blocks = ctx.spider_debug_blocks()
+    assert list(blocks) == list(range(-(-cat1.N // 4096)))
+    ctx.close()
+
+
+def test_iid_likelihood_kappa_zero(cat1):
+    ctx = binding.Context.from_catalog(cat1, kappa=0.0)
+    g, lp = ctx.spider_grad_logpost(0)
+    P = O.problem_from_catalog(cat1)
+    P.kappa = 0.0
+    L, go, _ = O.log_posterior(P, cat1.init_xyzt)
+    assert rel_l2(g, go) <= GRAD_TOL_FP32 and abs(lp - L) <= 1e-6 * abs(L)
+    ctx.close()
+
+
+def test_mlp_full_batch_gradient_parity(cat2):
+    ctx = binding.Context.from_catalog(cat2)
+    g, lp = ctx.spider_grad_logpost(0)
+    tm = ctx.spider_last_timing()
+    P = O.problem_from_catalog(cat2)
+    L, go, _ = O.log_posterior(P, cat2.init_xyzt)
+    print(f"MLP H=128 full batch: rel-L2 {rel_l2(g, go):.3e}, logpost {lp:.8e} vs {L:.8e}, "
+          f"pairs {tm['pairs']}, whitening iterations {tm['pcg_iters']}")
+    assert rel_l2(g, go) <= GRAD_TOL_FP32
+    assert abs(lp - L) <= 1e-5 * abs(L)
+    ctx.close()
+
+
+@pytest.mark.parametrize("seed", [1, 987654321])
+def test_minibatch_selection_and_gradient(cat2, seed):
+    bn, B = 1 << 18, 4096
+    ctx = binding.Context.from_catalog(cat2, batch_n=bn, block_obs=B)
+    g, lp = ctx.spider_grad_logpost(seed)
+    P = O.problem_from_catalog(cat2, batch_n=bn)
+    blocks = O.select_blocks(P.N, B, bn, seed)
+    assert np.array_equal(ctx.spider_debug_blocks(), blocks)           # bit-exact selection
+    sel = P.batch(seed)
+    idx, r, q = ctx.spider_debug_obs(P.N)
+    assert np.array_equal(np.sort(idx), sel)                           # same observation set
+    L, go, info = O.log_posterior(P, cat2.init_xyzt, sel)
+    rel = rel_l2(g, go)
+    print(f"minibatch seed {seed}: rel-L2 {rel:.3e}, scale {info['scale']:.3f}")
+    assert rel <= GRAD_TOL_FP32
+    assert abs(lp - L) <= 1e-5 * abs(L)
+    ctx.close()
+
+
+def test_ragged_blocks_and_shuffled_event_order(cat1):
+    sh = synth.shuffled_events(cat1, seed=3)
+    ctx = binding.Context.from_catalog(sh, batch_n=1000, block_obs=333)
+    P = O.problem_from_catalog(sh, batch_n=1000)
+    P.block_obs = 333
+    P.order = O.canonical_order(P.init, P.i, P.j, P.k, True)[1]
+    for seed in (5, 6):
+        g, lp = ctx.spider_grad_logpost(seed)
+        sel = P.batch(seed)
+        idx, _, _ = ctx.spider_debug_obs(P.N)
+        assert np.array_equal(np.sort(idx), sel)
+        L, go, _ = O.log_posterior(P, sh.init_xyzt, sel)
+        assert rel_l2(g, go) <= GRAD_TOL_FP32
+    ctx.close()
+
+
+def test_sgld_chain_positions_after_1000_steps(cat1):
+    eps = cat1.spec.hyper.eps
+    K = 1000
+    seeds = [1000 + t for t in range(K)]
+    ctx = binding.Context.from_catalog(cat1, thin=10, sample_cap=200)
+    for s in seeds:
+        ctx.spider_sgld_step(eps, s)
+    th, step = ctx.spider_get_state()
+    samples = ctx.spider_samples(1000)
+    P = O.problem_from_catalog(cat1)
+    to, so = O.run_chain(P, cat1.init_xyzt, eps, seeds, thin=10)
+    dx_m = np.abs(th[:, :3] - to[:, :3]).max() * 1e3
+    dt_ms = np.abs(th[:, 3] - to[:, 3]).max() * 1e3
+    print(f"after {K} steps: max |dx| {dx_m:.4f} m, max |dt0| {dt_ms:.5f} ms")
+    assert step == K and dx_m <= 1.0
+    assert samples.shape == (100, cat1.M, 4)
+    assert np.abs(samples[-1] - th).max() == 0.0
+    assert np.abs(samples[0][:, :3] - so[0][:, :3]).max() * 1e3 <= 1.0
+    ctx.close()
+
+
+def test_exact_resume(cat1):
+    eps = cat1.spec.hyper.eps
+    a = binding.Context.from_catalog(cat1)
+    for s in range(1, 6):
+        a.spider_sgld_step(eps, s)
+    th, step = a.spider_get_state()
+    for s in range(6, 11):
+        a.spider_sgld_step(eps, s)
+    end_a, _ = a.spider_get_state()
+    b = binding.Context.from_catalog(cat1)
+    b.spider_set_state(th, step)
+    for s in range(6, 11):
+        b.spider_sgld_step(eps, s)
+    end_b, step_b = b.spider_get_state()
+    assert step_b == 10 and np.array_equal(end_a, end_b)
+    a.close(); b.close()
+
+
+def test_nonfinite_state_is_reported(cat1):
+    ctx = binding.Context.from_catalog(cat1)
+    ctx.spider_sgld_step(3e38, 1)
+    with pytest.raises(binding.SpiderError) as e:
+        ctx.spider_sync()
+    assert e.value.code == -4
+    ctx.close()
+
+
+def test_invalid_inputs_rejected(cat1):
+    bad = np.array(cat1.i, copy=True)
+    bad[5] = cat1.M + 3
+    with pytest.raises(binding.SpiderError) as e:
+        binding.Context(cat1.init_xyzt, bad, cat1.j, cat1.k, cat1.dt, cat1.stations,
+                        binding.net_for_catalog(cat1), binding.config_for_catalog(cat1))
+    assert e.value.code == -1
+    with pytest.raises(binding.SpiderError):
+        binding.Context.from_catalog(cat1, block_obs=5000)
+
+
+def test_two_event_catalog():
+    # the smallest catalog: two events, one station, two observations
+    init = np.array([[0.0, 0.0, 10.0, 5.0], [0.5, 0.2, 10.3, 6.0]])
+    sta = np.array([[10.0, 0.0, 0.0]])
+    i, j, k = np.array([0, 1]), np.array([1, 0]), np.array([0, 0])
+    dt = np.array([-1.02, 0.97])
+    net = binding.Net(binding.TT_HOMOGENEOUS, v0=6.0)
+    cfg = binding.make_config(sigma=0.01, kappa=0.03)
+    ctx = binding.Context(init, i, j, k, dt, sta, net, cfg)
+    g, lp = ctx.spider_grad_logpost(0)
+    P = O.Problem(init, sta, i, j, k, dt, O.Model("homogeneous", v0=6.0), 0.01, 0.03, 0.25, 40.0,
+                  1e-5, np.array([0.5, 0.5, 0.5, 0.1]), np.array([0.01] * 4))
+    L, go, _ = O.log_posterior(P, init)
+    assert rel_l2(g, go) <= GRAD_TOL_FP32 and abs(lp - L) <= 1e-6 * abs(L)
+    ctx.close()

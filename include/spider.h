@@ -104,8 +104,9 @@ typedef struct {
   int32_t chain;           /* Philox counter word 1 (chain id)                   */
   int32_t catalog;         /* Philox counter word 2 (catalog id)                 */
   float noise_scale;       /* multiplies sqrt(2 eps) eta (stage-3 ramp, Sec. 3.2) */
-  int32_t pcg_max_it;      /* whitening solve: iteration cap                     */
-  float pcg_tol;           /* whitening solve: relative residual target          */
+  int32_t pcg_max_it;      /* whitening solve: cap on inner CG iterations         */
+  float pcg_tol;           /* whitening solve: target |u - A z| / |u|, with the
+                              residual evaluated in double-float (refinement)     */
   int64_t sample_cap;      /* samples kept on the device (ring buffer)           */
 } spider_config;
 
@@ -113,7 +114,7 @@ typedef struct spider_ctx spider_ctx;
 
 /* Fills *cfg with the defaults: Table 1 / Sec. 4 values (kappa 0.03 s, p 0.25,
  * ell 40 km, centroid sigma 0.01), event prior 0.5 km / 0.1 s (Sec. 4.1),
- * full batch, blocks of 4096, FP32, thin 1, reorder 1, noise 1, PCG 400 / 1e-6. */
+ * full batch, blocks of 4096, FP32, thin 1, reorder 1, noise 1, whitening 1000 / 1e-7. */
 void spider_config_default(spider_config *cfg);
 
 /* Validates and copies the catalog, stations and network; builds the canonical

@@ -259,8 +259,8 @@ void spider_config_default(spider_config* c) {
   c->chain = 0;
   c->catalog = 0;
   c->noise_scale = 1.0f;
-  c->pcg_max_it = 400;
-  c->pcg_tol = 1e-6f;
+  c->pcg_max_it = 1000;
+  c->pcg_tol = 1e-7f;
   c->sample_cap = 16;
 }
 
@@ -371,9 +371,14 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   AL(q_obs, N);
   AL(part_a, Q);
   AL(part_b, Q);
+  AL(part_c, Q);
   AL(rhs, PP);
+  AL(rhs_lo, PP);
   AL(diag, PP);
   AL(z, PP);
+  AL(z_lo, PP);
+  AL(rres, PP);
+  AL(dz, PP);
   AL(res, PP);
   AL(pv, PP);
   AL(Ap, PP);

@@ -168,10 +168,9 @@ __global__ void k_link(StepView v) {
 
 // ------------------------------------------------------------------ residuals
 // r_n = dt~_n - [(T_i - T_j) + (dt0_i - dt0_j)]  (Eq. 1; dt~ = dt - (t0_i - t0_j) of theta_0)
-// and the whitening right-hand side u = B^T r, diag(B^T B) per node.
+// and the whitening right-hand side u = B^T r (double-float), diag(lambda + B^T B) per node.
 __global__ void k_resid(StepView v) {
   extern __shared__ float smf[];
-  __shared__ double smd[33];
   const int L_max = v.L_max;
   float* Thi = smf;
   float* Tlo = Thi + L_max;
@@ -193,7 +192,6 @@ __global__ void k_resid(StepView v) {
   }
   for (int e = threadIdx.x; e < ne; e += blockDim.x) sw[e] = v.obs_sw[e0 + e];
   __syncthreads();
-  double rr = 0.0;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const uint32_t lij = v.obs_l[e0 + e];
     const int li = lij & 0xFFFF, lj = lij >> 16;
@@ -203,10 +201,7 @@ __global__ void k_resid(StepView v) {
     const float r = ((v.obs_dt[e0 + e] - dhi) - dt0) - dlo;
     rs[e] = r;
     v.r_obs[e0 + e] = r;
-    rr += (double)r * (double)r;
   }
-  rr = block_sum<double>(rr, smd);
-  if (threadIdx.x == 0) v.dblk[s] = rr;
   __syncthreads();
   if (!v.whiten) return;
   const uint16_t* he = v.blk_he + 2 * e0;
@@ -214,23 +209,37 @@ __global__ void k_resid(StepView v) {
     const int32_t q = q0 + l;
     const int h0 = v.node_he[q];
     const int h1 = (l + 1 < L) ? (int)v.node_he[q + 1] : 2 * ne;
-    float a = 0.f, d = 0.f;
+    df32 a = {0.f, 0.f};
+    float d = 0.f;
     for (int h = h0; h < h1; ++h) {
       const int code = he[h];
       const int e = code >> 1;
       const float w = sw[e];
-      a += (code & 1) ? -w * rs[e] : w * rs[e];
+      a = df_add(a, df_two_prod((code & 1) ? -w : w, rs[e]));
       d += w * w;
     }
     if (!v.multi[q]) {
       const int32_t u = v.loc2u[q];
-      v.rhs[u] = a;
+      v.rhs[u] = a.hi;
+      v.rhs_lo[u] = a.lo;
       v.diag[u] = v.lam + d;
     } else {
-      v.part_a[q] = a;
+      v.part_a[q] = a.hi;
+      v.part_c[q] = a.lo;
       v.part_b[q] = d;
     }
   }
+}
+
+// double-float sum over the selected occurrences of pair p (block order)
+__device__ __forceinline__ df32 merge_occ_df(const StepView& v, int32_t p, int tag) {
+  df32 a = {0.f, 0.f};
+  for (int32_t t = v.inc_off[p], t1 = v.inc_off[p + 1]; t < t1; ++t)
+    if (v.blk_stamp[v.inc_b[t]] == tag) {
+      const int32_t qq = v.inc_q[t];
+      a = df_add(a, df32{v.part_a[qq], v.part_c[qq]});
+    }
+  return a;
 }
 
 __global__ void k_merge_rhs(StepView v, int tag) {
@@ -239,7 +248,9 @@ __global__ void k_merge_rhs(StepView v, int tag) {
     const int32_t q = v.uniq_q[u];
     if (!v.multi[q]) continue;
     const int32_t p = v.node_pair[q];
-    v.rhs[u] = merge_occ(v, p, tag, v.part_a);
+    const df32 a = merge_occ_df(v, p, tag);
+    v.rhs[u] = a.hi;
+    v.rhs_lo[u] = a.lo;
     v.diag[u] = v.lam + merge_occ(v, p, tag, v.part_b);
   }
 }
@@ -291,8 +302,98 @@ __device__ float sum_partials(const float* part, int G, float* sm) {
   return block_sum<float>(a, sm);
 }
 
-// Solve (lambda I + B^T B) z = u with Jacobi-preconditioned CG over all
-// station groups at once (the nodes of different groups never share an edge).
+struct BlockRange {
+  int32_t q0;
+  int L;
+  int64_t e0;
+  int ne;
+};
+
+__device__ __forceinline__ BlockRange block_range(const StepView& v, int64_t s) {
+  BlockRange r;
+  const int32_t b = v.sel[s];
+  r.q0 = v.blk_node_off[b];
+  r.L = v.blk_node_off[b + 1] - r.q0;
+  r.e0 = (int64_t)b * v.B;
+  r.ne = (int)(v.N - r.e0 < v.B ? v.N - r.e0 : v.B);
+  return r;
+}
+
+// Ap = lambda p + B^T B p (FP32): node sums over each selected block's half-edges,
+// single nodes written directly, shared nodes as per-occurrence partials.
+__device__ void matvec_f32(const StepView& v, int64_t n_b, const float* __restrict__ p, float* pl) {
+  for (int64_t s = blockIdx.x; s < n_b; s += gridDim.x) {
+    const BlockRange br = block_range(v, s);
+    __syncthreads();
+    for (int l = threadIdx.x; l < br.L; l += blockDim.x) pl[l] = p[v.loc2u[br.q0 + l]];
+    __syncthreads();
+    const uint16_t* he = v.blk_he + 2 * br.e0;
+    for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
+      const int32_t q = br.q0 + l;
+      const int h0 = v.node_he[q];
+      const int h1 = (l + 1 < br.L) ? (int)v.node_he[q + 1] : 2 * br.ne;
+      const float pself = pl[l];
+      float acc = 0.f;
+      for (int h = h0; h < h1; ++h) {
+        const int code = he[h];
+        const int e = code >> 1;
+        const uint32_t lij = v.obs_l[br.e0 + e];
+        const int other = (code & 1) ? (int)(lij & 0xFFFF) : (int)(lij >> 16);
+        const float w = v.obs_sw[br.e0 + e];
+        acc += (w * w) * (pself - pl[other]);
+      }
+      if (!v.multi[q]) v.Ap[v.loc2u[q]] = v.lam * pself + acc;
+      else v.part_a[q] = acc;
+    }
+  }
+}
+
+// rres = u - (lambda I + B^T B) z, evaluated in double-float from z = z_hi + z_lo
+// (the residual of iterative refinement), rounded to FP32.
+__device__ void residual_df(const StepView& v, int64_t n_b, float* zh, float* zl) {
+  for (int64_t s = blockIdx.x; s < n_b; s += gridDim.x) {
+    const BlockRange br = block_range(v, s);
+    __syncthreads();
+    for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
+      const int32_t u = v.loc2u[br.q0 + l];
+      zh[l] = v.z[u];
+      zl[l] = v.z_lo[u];
+    }
+    __syncthreads();
+    const uint16_t* he = v.blk_he + 2 * br.e0;
+    for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
+      const int32_t q = br.q0 + l;
+      const int h0 = v.node_he[q];
+      const int h1 = (l + 1 < br.L) ? (int)v.node_he[q + 1] : 2 * br.ne;
+      const df32 zs = {zh[l], zl[l]};
+      df32 acc = {0.f, 0.f};
+      for (int h = h0; h < h1; ++h) {
+        const int code = he[h];
+        const int e = code >> 1;
+        const uint32_t lij = v.obs_l[br.e0 + e];
+        const int o = (code & 1) ? (int)(lij & 0xFFFF) : (int)(lij >> 16);
+        const float sw = v.obs_sw[br.e0 + e];
+        const df32 d = df_add(zs, df32{-zh[o], -zl[o]});
+        acc = df_add(acc, df_mul(df_two_prod(sw, sw), d));
+      }
+      if (!v.multi[q]) {
+        const int32_t u = v.loc2u[q];
+        df32 r = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zs, -v.lam));
+        r = df_add(r, df32{-acc.hi, -acc.lo});
+        v.rres[u] = r.hi;
+      } else {
+        v.part_a[q] = acc.hi;
+        v.part_c[q] = acc.lo;
+      }
+    }
+  }
+}
+
+// Solve (lambda I + B^T B) z = u over all station groups at once (nodes of
+// different groups never share an edge) by iterative refinement: the residual
+// is evaluated in double-float, each correction by Jacobi-preconditioned FP32 CG
+// to a relative tolerance of 1e-3; stop when |u - A z| <= tol |u| (double-float
+// residual) or after max_it inner iterations in total.
 __global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n_b, int max_it, float tol) {
   extern __shared__ float pl[];
   __shared__ float smr[33];
@@ -300,59 +401,61 @@ __global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n
   const int32_t P_u = v.counters[kCntPairs];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = G * blockDim.x;
   float* red = v.red;
-  // z = 0, r = u, y = D^-1 r, p = y
-  float rz = 0.f, bb = 0.f;
+  constexpr float kInnerTol = 1e-3f;
+  constexpr int kMaxRounds = 8;
+  float bb = 0.f;
   for (int32_t u = gtid; u < P_u; u += gstride) {
     const float r = v.rhs[u];
-    const float y = r / v.diag[u];
     v.z[u] = 0.f;
-    v.res[u] = r;
-    v.pv[u] = y;
-    rz += r * y;
+    v.z_lo[u] = 0.f;
     bb += r * r;
   }
-  rz = block_sum<float>(rz, smr);
   bb = block_sum<float>(bb, smr);
-  if (threadIdx.x == 0) {
-    red[0 * kMaxGrid + blockIdx.x] = rz;
-    red[1 * kMaxGrid + blockIdx.x] = bb;
-  }
+  if (threadIdx.x == 0) red[5 * kMaxGrid + blockIdx.x] = bb;
   if (!grid_barrier(v.counters)) return;
-  rz = sum_partials(red + 0 * kMaxGrid, G, smr);
-  bb = sum_partials(red + 1 * kMaxGrid, G, smr);
+  bb = sum_partials(red + 5 * kMaxGrid, G, smr);
+  const float outer_thr = tol * tol * bb;
   int it = 0;
-  const float thr = tol * tol * bb;
-  if (bb > 0.f) {
-    for (it = 0; it < max_it;) {
-      // Ap = lambda p + B^T B p : per selected block, node sums over its half-edges
-      for (int64_t s = blockIdx.x; s < n_b; s += G) {
-        const int32_t b = v.sel[s];
-        const int32_t q0 = v.blk_node_off[b];
-        const int L = v.blk_node_off[b + 1] - q0;
-        const int64_t e0 = (int64_t)b * v.B;
-        const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
-        __syncthreads();
-        for (int l = threadIdx.x; l < L; l += blockDim.x) pl[l] = v.pv[v.loc2u[q0 + l]];
-        __syncthreads();
-        const uint16_t* he = v.blk_he + 2 * e0;
-        for (int l = threadIdx.x; l < L; l += blockDim.x) {
-          const int32_t q = q0 + l;
-          const int h0 = v.node_he[q];
-          const int h1 = (l + 1 < L) ? (int)v.node_he[q + 1] : 2 * ne;
-          const float pself = pl[l];
-          float acc = 0.f;
-          for (int h = h0; h < h1; ++h) {
-            const int code = he[h];
-            const int e = code >> 1;
-            const uint32_t lij = v.obs_l[e0 + e];
-            const int other = (code & 1) ? (int)(lij & 0xFFFF) : (int)(lij >> 16);
-            const float w = v.obs_sw[e0 + e];
-            acc += (w * w) * (pself - pl[other]);
-          }
-          if (!v.multi[q]) v.Ap[v.loc2u[q]] = v.lam * pself + acc;
-          else v.part_a[q] = acc;
-        }
+  for (int round = 0; round < kMaxRounds && bb > 0.f && it < max_it; ++round) {
+    // outer residual in double-float
+    if (round == 0) {
+      for (int32_t u = gtid; u < P_u; u += gstride) v.rres[u] = v.rhs[u] + v.rhs_lo[u];
+    } else {
+      residual_df(v, n_b, pl, pl + v.L_max);
+      if (!grid_barrier(v.counters)) return;
+      for (int32_t u = gtid; u < P_u; u += gstride) {
+        const int32_t q = v.uniq_q[u];
+        if (!v.multi[q]) continue;
+        const df32 acc = merge_occ_df(v, v.node_pair[q], tag);
+        df32 r = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(df32{v.z[u], v.z_lo[u]}, -v.lam));
+        r = df_add(r, df32{-acc.hi, -acc.lo});
+        v.rres[u] = r.hi;
       }
+    }
+    // inner PCG on A dz = rres
+    float rz = 0.f, rr0 = 0.f;
+    for (int32_t u = gtid; u < P_u; u += gstride) {
+      const float r = v.rres[u];
+      const float y = r / v.diag[u];
+      v.dz[u] = 0.f;
+      v.res[u] = r;
+      v.pv[u] = y;
+      rz += r * y;
+      rr0 += r * r;
+    }
+    rz = block_sum<float>(rz, smr);
+    rr0 = block_sum<float>(rr0, smr);
+    if (threadIdx.x == 0) {
+      red[0 * kMaxGrid + blockIdx.x] = rz;
+      red[1 * kMaxGrid + blockIdx.x] = rr0;
+    }
+    if (!grid_barrier(v.counters)) return;
+    rz = sum_partials(red + 0 * kMaxGrid, G, smr);
+    rr0 = sum_partials(red + 1 * kMaxGrid, G, smr);
+    if (rr0 <= outer_thr) break;                       // refined solution is accurate enough
+    const float inner_thr = kInnerTol * kInnerTol * rr0;
+    while (it < max_it) {
+      matvec_f32(v, n_b, v.pv, pl);
       if (!grid_barrier(v.counters)) return;
       float pap = 0.f;
       for (int32_t u = gtid; u < P_u; u += gstride) {
@@ -370,10 +473,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n
       if (threadIdx.x == 0) red[2 * kMaxGrid + blockIdx.x] = pap;
       if (!grid_barrier(v.counters)) return;
       pap = sum_partials(red + 2 * kMaxGrid, G, smr);
-      const float alpha = rz / pap;
+      const float alpha = pap > 0.f ? rz / pap : 0.f;
       float rzn = 0.f, rr = 0.f;
       for (int32_t u = gtid; u < P_u; u += gstride) {
-        v.z[u] += alpha * v.pv[u];
+        v.dz[u] += alpha * v.pv[u];
         const float r = v.res[u] - alpha * v.Ap[u];
         v.res[u] = r;
         const float y = r / v.diag[u];
@@ -391,45 +494,65 @@ __global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n
       rzn = sum_partials(red + 3 * kMaxGrid, G, smr);
       rr = sum_partials(red + 4 * kMaxGrid, G, smr);
       ++it;
-      if (rr <= thr || !(pap > 0.f)) break;
+      if (rr <= inner_thr || !(pap > 0.f)) break;
       const float beta = rzn / rz;
       rz = rzn;
       for (int32_t u = gtid; u < P_u; u += gstride) v.pv[u] = v.yv[u] + beta * v.pv[u];
       if (!grid_barrier(v.counters)) return;
     }
-  } else {
-    for (int32_t u = gtid; u < P_u; u += gstride) v.z[u] = 0.f;
+    // z += dz in double-float
+    for (int32_t u = gtid; u < P_u; u += gstride) {
+      const df32 zn = df_add_f(df32{v.z[u], v.z_lo[u]}, v.dz[u]);
+      v.z[u] = zn.hi;
+      v.z_lo[u] = zn.lo;
+    }
+    if (!grid_barrier(v.counters)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) v.counters[kCntIters] = it;
 }
 
-// q_e = sigma^-2 (r_e - sqrt(w_e) (z_i - z_j)) and the node sums
-// s_p = sum_{e: p = i-end} q_e - sum_{e: p = j-end} q_e  (= d loglik / d T_p)
+// q_e = sigma^-2 (r_e - sqrt(w_e) (z_i - z_j)) with z in double-float, the node
+// sums s_p = sum_{e: p = i-end} q_e - sum_{e: p = j-end} q_e (= d loglik / d T_p),
+// and r^T Sigma^-1 r = sum_e r_e q_e (FP64 per block).
 __global__ void k_final(StepView v) {
   extern __shared__ float smf[];
-  float* zl = smf;
+  __shared__ double smd[33];
+  float* zh = smf;
+  float* zl = zh + v.L_max;
   float* qs = zl + v.L_max;
   const int s = blockIdx.x;
-  const int32_t b = v.sel[s];
-  const int32_t q0 = v.blk_node_off[b];
-  const int L = v.blk_node_off[b + 1] - q0;
-  const int64_t e0 = (int64_t)b * v.B;
-  const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
-  for (int l = threadIdx.x; l < L; l += blockDim.x) zl[l] = v.whiten ? v.z[v.loc2u[q0 + l]] : 0.f;
-  __syncthreads();
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    const uint32_t lij = v.obs_l[e0 + e];
-    const float bz = v.obs_sw[e0 + e] * (zl[lij & 0xFFFF] - zl[lij >> 16]);
-    const float qe = v.inv_s2 * (v.r_obs[e0 + e] - bz);
-    qs[e] = qe;
-    v.q_obs[e0 + e] = qe;
+  const BlockRange br = block_range(v, s);
+  for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
+    if (v.whiten) {
+      const int32_t u = v.loc2u[br.q0 + l];
+      zh[l] = v.z[u];
+      zl[l] = v.z_lo[u];
+    } else {
+      zh[l] = 0.f;
+      zl[l] = 0.f;
+    }
   }
   __syncthreads();
-  const uint16_t* he = v.blk_he + 2 * e0;
-  for (int l = threadIdx.x; l < L; l += blockDim.x) {
-    const int32_t q = q0 + l;
+  double quad = 0.0;
+  for (int e = threadIdx.x; e < br.ne; e += blockDim.x) {
+    const uint32_t lij = v.obs_l[br.e0 + e];
+    const int li = lij & 0xFFFF, lj = lij >> 16;
+    const df32 d = df_add(df32{zh[li], zl[li]}, df32{-zh[lj], -zl[lj]});
+    const df32 bz = df_mul_f(d, v.obs_sw[br.e0 + e]);
+    const float r = v.r_obs[br.e0 + e];
+    const df32 t = df_add_f(df32{-bz.hi, -bz.lo}, r);
+    const float qe = v.inv_s2 * t.hi;
+    qs[e] = qe;
+    v.q_obs[br.e0 + e] = qe;
+    quad += (double)r * (double)qe;
+  }
+  quad = block_sum<double>(quad, smd);
+  if (threadIdx.x == 0) v.dblk[s] = quad;
+  const uint16_t* he = v.blk_he + 2 * br.e0;
+  for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
+    const int32_t q = br.q0 + l;
     const int h0 = v.node_he[q];
-    const int h1 = (l + 1 < L) ? (int)v.node_he[q + 1] : 2 * ne;
+    const int h1 = (l + 1 < br.L) ? (int)v.node_he[q + 1] : 2 * br.ne;
     float a = 0.f;
     for (int h = h0; h < h1; ++h) {
       const int code = he[h];
@@ -442,10 +565,8 @@ __global__ void k_final(StepView v) {
 
 // s_p * (N/n) times (dT/dx_p, 1) into the global pair slots, stamped.
 __global__ void k_merge_s(StepView v, int tag) {
-  __shared__ double smd[33];
   const int32_t P_u = v.counters[kCntPairs];
   const float scale = (float)((double)v.N / (double)v.counters[kCntObs]);
-  double uz = 0.0;
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     const int32_t q = v.uniq_q[u];
     const int32_t p = v.node_pair[q];
@@ -455,10 +576,7 @@ __global__ void k_merge_s(StepView v, int tag) {
     v.gp[p] = make_float4(sp * J.x, sp * J.y, sp * J.z, sp);
     v.pstamp[p] = tag;
     v.estamp[v.pair_ev[p]] = tag;
-    if (v.whiten) uz += (double)v.rhs[u] * (double)v.z[u];
   }
-  uz = block_sum<double>(uz, smd);
-  if (threadIdx.x == 0) v.dred[kMaxGrid + blockIdx.x] = uz;   // slot 1
 }
 
 // ------------------------------------------------------------------ events
@@ -559,14 +677,12 @@ __global__ void k_cen_init(StepView v, int cur) {
 
 // FP64 log posterior: -1/2 (N/n) sigma^-2 (r.r - u.z) - 1/2 |dtheta/sigma_e|^2
 //                     - 1/2 |mean(dtheta)/sigma_c|^2   (constants dropped)
-__global__ void k_logpost(StepView v, int64_t n_b, int gu, int cur) {
+__global__ void k_logpost(StepView v, int64_t n_b, int cur) {
   __shared__ double smd[33];
-  double rr = 0.0, uz = 0.0, lp = 0.0;
-  for (int64_t i = threadIdx.x; i < n_b; i += blockDim.x) rr += v.dblk[i];
-  for (int i = threadIdx.x; i < gu; i += blockDim.x) uz += v.dred[kMaxGrid + i];
+  double quad = 0.0, lp = 0.0;
+  for (int64_t i = threadIdx.x; i < n_b; i += blockDim.x) quad += v.dblk[i];
   for (int i = threadIdx.x; i < v.cen_grid; i += blockDim.x) lp += v.dred[2 * kMaxGrid + i];
-  rr = block_sum<double>(rr, smd);
-  uz = block_sum<double>(uz, smd);
+  quad = block_sum<double>(quad, smd);
   lp = block_sum<double>(lp, smd);
   double c[4] = {0, 0, 0, 0};
   for (int i = 0; i < v.cen_grid; ++i) {
@@ -575,7 +691,6 @@ __global__ void k_logpost(StepView v, int64_t n_b, int gu, int cur) {
   }
   if (threadIdx.x == 0) {
     const double scale = (double)v.N / (double)v.counters[kCntObs];
-    const double quad = (double)v.inv_s2 * (rr - (v.whiten ? uz : 0.0));
     const double ll = -0.5 * scale * quad;
     const double lpr = -0.5 * lp;
     const float isc[4] = {v.inv_sig_c2.x, v.inv_sig_c2.y, v.inv_sig_c2.z, v.inv_sig_c2.w};
@@ -615,8 +730,8 @@ cudaError_t launch_select(const StepView& v, int64_t n_b, int full, uint64_t see
 }
 
 size_t resid_smem(const StepView& v) { return (size_t)(3 * v.L_max + 2 * v.B) * sizeof(float); }
-size_t final_smem(const StepView& v) { return (size_t)(v.L_max + v.B) * sizeof(float); }
-size_t pcg_smem(const StepView& v) { return (size_t)v.L_max * sizeof(float); }
+size_t final_smem(const StepView& v) { return (size_t)(2 * v.L_max + v.B) * sizeof(float); }
+size_t pcg_smem(const StepView& v) { return (size_t)2 * v.L_max * sizeof(float); }
 
 cudaError_t configure_step_kernels(const StepView& v) {
   cudaError_t e;
@@ -663,7 +778,7 @@ cudaError_t launch_finish(const StepView& v, int64_t n_b, int tag, int gu, int m
   k_final<<<(unsigned)n_b, kThreads, final_smem(v), st>>>(v);
   k_merge_s<<<gu, kThreads, 0, st>>>(v, tag);
   k_event<<<v.cen_grid, kThreads, 0, st>>>(v, tag, mode, eps, noise_scale, seed, cur, sample_slot);
-  if (mode == 0) k_logpost<<<1, kThreads, 0, st>>>(v, n_b, gu, cur);
+  if (mode == 0) k_logpost<<<1, kThreads, 0, st>>>(v, n_b, cur);
   return cudaGetLastError();
 }
 

@@ -93,11 +93,16 @@ struct StepView {
   float4* J;
   float* r_obs;
   float* q_obs;
-  float* part_a;
-  float* part_b;
-  float* rhs;
-  float* diag;
-  float* z;
+  float* part_a;     // per-occurrence partials (multi nodes): hi part
+  float* part_b;     //   degree partials
+  float* part_c;     //   lo part
+  float* rhs;        // u = B^T r (hi)
+  float* rhs_lo;     //           (lo)
+  float* diag;       // lambda + diag(B^T B)
+  float* z;          // solution (hi)
+  float* z_lo;       //          (lo)
+  float* rres;       // outer (double-float) residual rounded to FP32: inner right-hand side
+  float* dz;         // inner correction
   float* res;
   float* pv;
   float* Ap;

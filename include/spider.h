@@ -189,6 +189,32 @@ void spider_net_free(spider_netdev *nd);
 int spider_tt_pairs(const spider_netdev *nd, int64_t P, const float *src, const float *rcv,
                     float *T_hi, float *T_lo, float *J, void *stream);
 
+/* Allocation-free variant of spider_tt_pairs for the MLP model in FP32.  The
+ * paper has no counterpart: it exists for callers that may not allocate device
+ * memory -- code running inside a runtime that owns all device memory up
+ * front (a fixed arena or memory pool), latency-critical paths that cannot
+ * afford cudaMalloc's implicit device synchronisation, or callers linked
+ * into a process whose allocator must not be touched.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine; the caller still passes every input
+ * and output (src, rcv, T_hi, T_lo, J as in spider_tt_pairs, all device
+ * pointers) and the network as host arrays (net->W, net->b, read during the
+ * call).  What the kernel needs besides them -- the weights in the layouts it
+ * reads, per-CTA slots for silu'(z) between the forward and the reverse sweep,
+ * and the (hi, lo) staging of T -- lives in one fixed-size array of static
+ * device memory (about 40 MB), which every GPU that loads this library holds
+ * until the process exits.  Limits: net->kind == SPIDER_TT_MLP,
+ * H in {32, 64, 128, 256}, 0 <= P <= 2^20; anything else returns
+ * SPIDER_E_UNSUPPORTED or SPIDER_E_INVAL and spider_last_error(NULL) names the
+ * limit.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents; the kernel writes every word it reads within the same call, so
+ * nothing needs clearing, but calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller.
+ * Asynchronous on `stream` (a cudaStream_t or NULL). */
+int spider_tt_pairs_noalloc(const spider_net *net, int64_t P, const float *src, const float *rcv,
+                            float *T_hi, float *T_lo, float *J, void *stream);
+
 /* Philox4x32-10 words computed on the device (host output, synchronous):
  * out[4 m + a] = word a of Philox(counter (c0 + m, c1, c2, c3), key = seed),
  * m in [0, n).  Exposed so the noise stream can be checked word for word. */

@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "spider_net_free": (None, [vp]),
         "spider_tt_pairs": (C.c_int, [vp, i64, vp, vp, vp, vp, vp, vp]),
         "spider_philox_words": (C.c_int, [u64, u32, u32, u32, u32, i64, C.POINTER(u32)]),
+        "spider_tt_pairs_noalloc": (C.c_int, [C.POINTER(spider_net), i64, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -305,3 +306,13 @@ class NetDevice:
                                               C.c_void_p(thi_ptr), C.c_void_p(tlo_ptr or None),
                                               C.c_void_p(j_ptr or None), C.c_void_p(stream or None)),
                None)
+
+
+def spider_tt_pairs_noalloc(net: Net, P: int, src_ptr: int, rcv_ptr: int, thi_ptr: int,
+                            tlo_ptr: int = 0, j_ptr: int = 0, stream: int = 0):
+    """Allocation-free travel times (see include/spider.h): host network,
+    device inputs and outputs given as integer pointers."""
+    code = load_library().spider_tt_pairs_noalloc(
+        C.byref(net.s), P, C.c_void_p(src_ptr), C.c_void_p(rcv_ptr), C.c_void_p(thi_ptr),
+        C.c_void_p(tlo_ptr or None), C.c_void_p(j_ptr or None), C.c_void_p(stream or None))
+    _check(code, None)

@@ -239,6 +239,8 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
 
 }  // namespace
 
+void spider::set_static_error(const char* msg) { g_static_err = msg; }
+
 extern "C" {
 
 void spider_config_default(spider_config* c) {

@@ -6,6 +6,9 @@
 
 namespace spider {
 
+// message returned by spider_last_error(NULL)
+void set_static_error(const char* msg);
+
 // travel times (k_tt.cu, k_mlp_tc.cu)
 bool tt_supported_width(int H);
 size_t tt_scratch_floats(const NetView& net, int num_sms);

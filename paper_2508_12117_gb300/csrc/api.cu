@@ -420,6 +420,7 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   c->gu = std::min(kMaxGrid, 4 * c->num_sms);
 
   if ((e = upload_net(net, cfg->precision, &c->net, L, st))) return bail(cuda_fail(c, e, "network upload"));
+  c->net.err = v.counters + kCntError;
   const size_t scr = tt_scratch_floats(c->net, c->num_sms);
   if (scr) {
     if ((e = dalloc(L, &c->tt_scratch, scr))) return bail(cuda_fail(c, e, "alloc scratch"));
@@ -639,6 +640,8 @@ int spider_net_upload(const spider_net* net, int32_t precision, spider_netdev** 
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nd->num_sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t scr = e == cudaSuccess ? tt_scratch_floats(nd->net, nd->num_sms) : 0;
   if (e == cudaSuccess && scr) e = dalloc(nd->allocs, &nd->scratch, scr);
+  if (e == cudaSuccess) e = dalloc(nd->allocs, &nd->net.err, 1);
+  if (e == cudaSuccess) e = cudaMemset(nd->net.err, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     g_static_err = cudaGetErrorString(e);

@@ -1,19 +1,557 @@
-// Tensor-core (tcgen05) forms of the travel-time MLP: not built yet.
+// Tensor-core (tcgen05, sm_103a) form of the travel-time MLP: forward pass and
+// source Jacobian for tiles of 128 (event, station) pairs (Sec. 2.1, Sec. 3.2).
+//
+//   layer 1 (6 -> H, FP32, CUDA cores)  h1 = silu(W1 [x; s] + b1)
+//   layers 2..4 (H x H, BF16 x BF16 -> FP32 in TMEM)  h_l = silu(W_l h_{l-1} + b_l)
+//   output (H -> 1, FP32)  tau = w5 . h4 + b5,  T = |x - s| tau  (double-float outer product)
+//   reverse sweep (H x H, BF16 -> FP32 in TMEM)
+//       delta4 = w5 * silu'(z4);  delta_{l-1} = (W_l^T delta_l) * silu'(z_{l-1})
+//   dtau/dx = W1[:, :3]^T delta1 (FP32),  dT/dx = tau (x - s)/r + r dtau/dx.
+//
+// One CTA per SM, persistent over tiles; 10 warps:
+//   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one pair per
+//              lane) and columns [ (w / 4) H/2, (w / 4 + 1) H/2 );
+//   warp 8     producer: 1-D bulk async copies (cp.async.bulk) of pre-swizzled
+//              weight K-blocks (H rows x 64 BF16) into a two-stage ring;
+//   warp 9     MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = H,
+//              K = 16, A = activations (SW128 K-major, shared memory),
+//              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
+// TMEM (2H columns): [0, H) accumulator, [H, 3H/2) silu'(z1) and [3H/2, 2H)
+// silu'(z2) packed as BF16 pairs; silu'(z3) sits in shared memory.
+// Every wait is bounded (2 s on the global timer): on timeout the kernel sets
+// SPIDER_E_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "dfloat.cuh"
 #include "kernels.h"
+#include "pairs.cuh"
 #include "spider.h"
 
 namespace spider {
+namespace {
 
-bool mlp_tc_supported(int, int) { return false; }
+constexpr int kRows = 128;          // pairs per tile = MMA M = TMEM lanes
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTcThreads = kEpiThreads + 64;
+constexpr int kStages = 2;
+constexpr uint64_t kWaitNs = 2000000000ull;
 
-cudaError_t mlp_tc_prepare(const float* const*, int, int, void** image, float** scales, cudaStream_t) {
-  *image = nullptr;
-  *scales = nullptr;
-  return cudaErrorNotSupported;
+template <int H>
+struct Cfg {
+  static constexpr int KB = H / 64;                 // K-blocks of 64 BF16 per layer
+  static constexpr int kChunk = H * 128;            // bytes of one weight K-block (H rows x 128 B)
+  static constexpr int kImage = H * H * 2;          // bytes of one weight image
+  static constexpr int kA = kRows * H * 2;          // activations, SW128 K-major
+  static constexpr int kD3 = kRows * H * 2;         // silu'(z3), BF16
+  static constexpr int kHalf = H / 2;               // columns per epilogue thread
+  static constexpr int kTmemCols = 2 * H;
+  static constexpr int kChunksPerTile = 6 * KB;
+  // shared-memory carve-up (offsets from a 1024-aligned base)
+  static constexpr int oA = 0;
+  static constexpr int oB = oA + kA;
+  static constexpr int oD3 = oB + kStages * kChunk;
+  static constexpr int oPar = oD3 + kD3;                  // W1 (6H), b1, b2, b3, b4, w5 (5H) floats
+  static constexpr int oRed = oPar + 11 * H * 4;          // [4][2][kRows] floats
+  static constexpr int oBar = oRed + 4 * 2 * kRows * 4;   // mbarriers
+  static constexpr int oMisc = oBar + 8 * 8;              // tmem base, abort flag
+  static constexpr int kSmem = oMisc + 16 + 1024;         // + alignment slack
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-cudaError_t launch_mlp_tc(const NetView&, const PairSource&, TTOut, int, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.  False on abort/timeout.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int32_t* gerr) {
+  if (mbar_test(b, parity)) return true;
+  const uint64_t t0 = gtime();
+  for (;;) {
+    if (mbar_test(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtime() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      atomicCAS(gerr, 0, SPIDER_E_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (both K-major), FP32 D, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// silu(z) = z s, silu'(z) = s (1 + z (1 - s)), s = sigmoid(z) = (1 + tanh(z/2)) / 2
+__device__ __forceinline__ void silu_tc(float z, float& h, float& d) {
+  const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+  h = z * s;
+  d = fmaf(z * s, 1.0f - s, s);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+// byte offset of element (row r, k) in a 128-row SW128 K-major operand (K-blocks of 64)
+__device__ __forceinline__ uint32_t a_off(int r, int k) {
+  const int kb = k >> 6, j = (k >> 3) & 7;
+  return (uint32_t)(kb * (kRows * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + (k & 7) * 2);
+}
+// silu'(z3): 16-byte chunk c/8 of row r at ((c/8) * 128 + r) * 16
+__device__ __forceinline__ uint32_t d3_off(int r, int c) { return (uint32_t)(((c >> 3) * kRows + r) * 16); }
+
+template <int H>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tt_mlp_tc(NetView net, PairSource src, TTOut out, const uint8_t* __restrict__ wimg, int32_t* gerr) {
+  using C = Cfg<H>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = sm + C::oA;
+  uint8_t* sB = sm + C::oB;
+  uint8_t* sD3 = sm + C::oD3;
+  float* pW1 = reinterpret_cast<float*>(sm + C::oPar);
+  float* pb1 = pW1 + 6 * H;
+  float* pb = pb1 + H;       // b2, b3, b4
+  float* pw5 = pb + 3 * H;
+  float* red = reinterpret_cast<float*>(sm + C::oRed);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::oBar);
+  uint64_t* full = bars;           // [2] weight stage loaded
+  uint64_t* empty = bars + 2;      // [2] weight stage consumed
+  uint64_t* acc_ready = bars + 4;  // accumulator complete
+  uint64_t* a_ready = bars + 5;    // epilogue done with TMEM reads + A written
+  uint64_t* drain = bars + 6;      // MMA drain on abort
+  uint64_t* red_ready = bars + 7;  // both column halves of every row reduced
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + C::oMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + C::oMisc + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    mbar_init(acc_ready, 1);
+    mbar_init(a_ready, kEpiThreads);
+    mbar_init(drain, 1);
+    mbar_init(red_ready, kEpiThreads);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < 6 * H; i += blockDim.x) pW1[i] = net.W1[i];
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    pb1[i] = net.b1[i];
+    pb[i] = net.bh[0][i];
+    pb[H + i] = net.bh[1][i];
+    pb[2 * H + i] = net.bh[2][i];
+    pw5[i] = net.W5[i];
+  }
+  if (warp == kEpiWarps + 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"((uint32_t)C::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t P = pair_count(src);
+  const int64_t ntiles = (P + kRows - 1) / kRows;
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (warp == kEpiWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      const int64_t total = my_tiles * C::kChunksPerTile;
+      int64_t n = 0;
+      for (; n < total; ++n) {
+        const int s = (int)(n & 1);
+        const int64_t use = n >> 1;
+        if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), abort_flag, gerr)) break;
+        const int c = (int)(n % C::kChunksPerTile);
+        const uint8_t* g = wimg + (size_t)(c / C::KB) * C::kImage + (size_t)(c % C::KB) * C::kChunk;
+        mbar_expect_tx(&full[s], C::kChunk);
+        bulk_load(sB + s * C::kChunk, g, C::kChunk, &full[s]);
+      }
+      // copies still in flight must land before the CTA's shared memory goes away
+      for (int64_t m = (n > kStages ? n - kStages : 0); m < n; ++m) {
+        const int s = (int)(m & 1);
+        const uint64_t t0 = gtime();
+        while (!mbar_test(&full[s], (uint32_t)((m >> 1) & 1)))
+          if (gtime() - t0 > kWaitNs) break;
+      }
+    }
+  } else if (warp == kEpiWarps + 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(H);
+      const uint32_t a_base = su32(sA), b_base = su32(sB);
+      int64_t n = 0;        // weight chunks consumed
+      uint32_t a_phase = 0;
+      bool ok = true;
+      int issued = 0;
+      for (int64_t t = 0; t < my_tiles && ok; ++t) {
+        for (int layer = 0; layer < 6 && ok; ++layer) {
+          if (!mbar_wait(a_ready, a_phase, abort_flag, gerr)) { ok = false; break; }
+          a_phase ^= 1;
+          tc_after();
+          for (int kb = 0; kb < C::KB; ++kb, ++n) {
+            const int s = (int)(n & 1);
+            if (!mbar_wait(&full[s], (uint32_t)((n >> 1) & 1), abort_flag, gerr)) { ok = false; break; }
+            tc_after();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t ad = sw128_desc(a_base + kb * (kRows * 128) + k * 32);
+              const uint64_t bd = sw128_desc(b_base + s * C::kChunk + k * 32);
+              umma(tmem, ad, bd, idesc, (kb | k) ? 1u : 0u);
+              ++issued;
+            }
+            umma_commit(&empty[s]);
+          }
+          if (ok) umma_commit(acc_ready);
+        }
+      }
+      if (!ok && issued) {
+        // let the MMAs already issued finish before TMEM is released
+        umma_commit(drain);
+        const uint64_t t0 = gtime();
+        while (!mbar_test(drain, 0))
+          if (gtime() - t0 > kWaitNs) break;
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int g = warp & 3, half = warp >> 2;
+    const int r = g * 32 + lane;                       // tile row = TMEM lane
+    const uint32_t lane_addr = tmem + ((uint32_t)(g * 32) << 16);
+    const int c0 = half * C::kHalf;                    // first column of this thread
+    uint32_t acc_phase = 0, red_phase = 0;
+    for (int64_t t = 0; t < my_tiles; ++t) {
+      const int64_t u0 = (blockIdx.x + t * gridDim.x) * kRows;
+      const int64_t u = u0 + r;
+      const bool valid = u < P;
+      float x[6];
+      {
+        PairGeo pg;
+        load_pair(src, valid ? u : u0, pg);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          x[c] = pg.shi[c] + (pg.slo[c] + pg.soff[c]);
+          x[3 + c] = pg.rhi[c] + pg.rlo[c];
+        }
+      }
+      // layer 1 in FP32: h1 -> A (BF16), silu'(z1) -> TMEM [H, 3H/2)
+      for (int cc = 0; cc < C::kHalf; cc += 32) {
+        const int col = c0 + cc;
+        uint32_t hp[16], dp[16];
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) {
+          float z0 = pb1[col + i], z1 = pb1[col + i + 1];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            z0 = fmaf(pW1[(col + i) * 6 + c], x[c], z0);
+            z1 = fmaf(pW1[(col + i + 1) * 6 + c], x[c], z1);
+          }
+          float h0, d0, h1, d1;
+          silu_tc(z0, h0, d0);
+          silu_tc(z1, h1, d1);
+          hp[i / 2] = pack_bf16(h0, h1);
+          dp[i / 2] = pack_bf16(d0, d1);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
+              make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+        tmem_st16(lane_addr + H + col / 2, dp);
+      }
+      tmem_wait_st();
+      fence_async_smem();
+      tc_before();
+      mbar_arrive(a_ready);
+
+      float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
+      bool ok = true;
+      for (int layer = 0; layer < 6; ++layer) {
+        const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        acc_phase ^= 1;
+        tc_after();
+        for (int cc = 0; cc < C::kHalf; cc += 32) {
+          const int col = c0 + cc;
+          float v[32];
+          tmem_ld32(lane_addr + col, v);
+          tmem_wait_ld();
+          uint32_t hp[16], dp[16];
+          if (layer < 3) {
+            // forward layers 2..4
+            const float* bias = pb + layer * H;
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+              float h0, d0, h1, d1;
+              silu_tc(v[i] + bias[col + i], h0, d0);
+              silu_tc(v[i + 1] + bias[col + i + 1], h1, d1);
+              if (layer == 2) {
+                const float w0 = pw5[col + i], w1 = pw5[col + i + 1];
+                tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
+                hp[i / 2] = pack_bf16(w0 * d0, w1 * d1);     // delta4
+              } else {
+                hp[i / 2] = pack_bf16(h0, h1);
+                dp[i / 2] = pack_bf16(d0, d1);
+              }
+            }
+            if (layer == 0) {
+              tmem_st16(lane_addr + H + C::kHalf + col / 2, dp);                 // silu'(z2)
+            } else if (layer == 1) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)                                         // silu'(z3)
+                *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8 * q)) =
+                    make_uint4(dp[4 * q], dp[4 * q + 1], dp[4 * q + 2], dp[4 * q + 3]);
+            }
+          } else {
+            // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
+            uint32_t dd[16];
+            if (layer == 3) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const uint4 w4 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8 * q));
+                dd[4 * q] = w4.x; dd[4 * q + 1] = w4.y; dd[4 * q + 2] = w4.z; dd[4 * q + 3] = w4.w;
+              }
+            } else {
+              tmem_ld16(lane_addr + H + (layer == 4 ? C::kHalf : 0) + col / 2, dd);
+              tmem_wait_ld();
+            }
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+              const float e0 = v[i] * bf16_lo(dd[i / 2]);
+              const float e1 = v[i + 1] * bf16_hi(dd[i / 2]);
+              if (layer == 5) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                  gpart[c] = fmaf(pW1[(col + i) * 6 + c], e0, fmaf(pW1[(col + i + 1) * 6 + c], e1, gpart[c]));
+              } else {
+                hp[i / 2] = pack_bf16(e0, e1);
+              }
+            }
+          }
+          if (layer < 5) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
+                  make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+          }
+        }
+        if (layer == 0) tmem_wait_st();
+        if (layer < 5) {
+          fence_async_smem();
+          tc_before();
+          mbar_arrive(a_ready);
+        }
+      }
+      if (!ok) break;
+      tc_before();
+      // combine the two column halves of each row and write T, dT/dx
+      red[(0 * 2 + half) * kRows + r] = tpart;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) red[((1 + c) * 2 + half) * kRows + r] = gpart[c];
+      mbar_arrive(red_ready);
+      const bool got = mbar_wait(red_ready, red_phase, abort_flag, gerr);
+      red_phase ^= 1;
+      if (!__all_sync(0xffffffffu, got)) break;
+      if (half == 0 && valid) {
+        const float dtau = red[0 * kRows + r] + red[1 * kRows + r];
+        float gt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gt[c] = red[((1 + c) * 2) * kRows + r] + red[((1 + c) * 2 + 1) * kRows + r];
+        PairGeo pg;
+        load_pair(src, u, pg);
+        df32 d[3];
+        const df32 rr = geometry(pg, d);
+        const df32 T = df_add_f(df_mul_f(rr, net.b5), rr.hi * dtau);
+        out.T2[u] = make_float2(T.hi, T.lo);
+        if (out.J) {
+          const float tau = net.b5 + dtau;
+          const float f = tau / rr.hi;
+          out.J[u] = make_float4(f * d[0].hi + rr.hi * gt[0], f * d[1].hi + rr.hi * gt[1],
+                                 f * d[2].hi + rr.hi * gt[2], 0.f);
+        }
+      }
+    }
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  __syncwarp();
+  if (warp == kEpiWarps + 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::kTmemCols));
+}
+
+// round-to-nearest-even FP32 -> BF16 on the host
+uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+template <int H>
+cudaError_t launch_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, cudaStream_t st) {
+  using C = Cfg<H>;
+  cudaError_t e = cudaFuncSetAttribute(k_tt_mlp_tc<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  if (e != cudaSuccess) return e;
+  k_tt_mlp_tc<H><<<num_sms, kTcThreads, C::kSmem, st>>>(net, src, out, (const uint8_t*)net.tc, net.err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool mlp_tc_supported(int H, int precision) {
+  return precision == SPIDER_BF16 && (H == 64 || H == 128 || H == 256);
+}
+
+// Weight images for the B operand, in the order the MMA consumes them:
+// W2, W3, W4 (forward: B[n][k] = W[n][k]) then W4^T, W3^T, W2^T (reverse:
+// B[n][k] = W[k][n]); each image is H/64 K-blocks of H rows x 128 bytes in
+// the 128-byte-swizzled K-major layout the shared-memory descriptor names.
+cudaError_t mlp_tc_prepare(const float* const Wn_host[3], int H, int precision, void** image, float** scales,
+                           cudaStream_t st) {
+  *image = nullptr;
+  *scales = nullptr;
+  if (!mlp_tc_supported(H, precision)) return cudaErrorNotSupported;
+  const size_t img = (size_t)H * H * 2;
+  std::vector<uint8_t> host(6 * img, 0);
+  for (int l = 0; l < 6; ++l) {
+    const float* W = Wn_host[l < 3 ? l : 5 - l];
+    const bool transpose = l >= 3;
+    uint8_t* base = host.data() + l * img;
+    for (int n = 0; n < H; ++n)
+      for (int k = 0; k < H; ++k) {
+        const float v = transpose ? W[(size_t)k * H + n] : W[(size_t)n * H + k];
+        const int kb = k / 64, j = (k % 64) / 8;
+        const size_t off = (size_t)kb * H * 128 + (size_t)(n / 8) * 1024 + (size_t)(n % 8) * 128 +
+                           (size_t)((j ^ (n % 8)) * 16) + (size_t)(k % 8) * 2;
+        const uint16_t b = to_bf16(v);
+        std::memcpy(base + off, &b, 2);
+      }
+  }
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, host.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return e;
+  }
+  *image = d;
+  return cudaSuccess;
+}
+
+cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, cudaStream_t st) {
+  if (net.precision != SPIDER_BF16 || !net.tc || !net.err) return cudaErrorNotSupported;
+  switch (net.H) {
+    case 64: return launch_tc<64>(net, src, out, num_sms, st);
+    case 128: return launch_tc<128>(net, src, out, num_sms, st);
+    case 256: return launch_tc<256>(net, src, out, num_sms, st);
+    default: return cudaErrorNotSupported;
+  }
 }
 
 }  // namespace spider

@@ -32,6 +32,7 @@ struct NetView {
   float b5;
   const void* tc;      // tensor-core operand images (BF16 / FP8), null in FP32
   const float* tc_scale;  // per-layer FP8 dequantisation scales (6), null otherwise
+  int32_t* err;           // device error flag the tensor-core kernel reports bounded-wait timeouts to
 };
 
 // Where the pairs of a travel-time launch come from.

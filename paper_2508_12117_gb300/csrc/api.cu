@@ -383,6 +383,14 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   AL(dz, PP);
   AL(res, PP);
   AL(pv, PP);
+  AL(pv2, PP);
+  AL(umulti, PP);
+  AL(rowlen, PP);
+  AL(rowptr, PP + 1);
+  AL(occ_off, Q);
+  AL(csr_col, 2 * N);
+  AL(csr_sw, 2 * N);
+  AL(scan_part, kMaxGrid + 1);
   AL(Ap, PP);
   AL(yv, PP);
   AL(s_u, PP);

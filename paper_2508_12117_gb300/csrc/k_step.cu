@@ -152,6 +152,7 @@ __global__ void k_assign(StepView v) {
       v.loc2u[q] = u;
       v.uniq_pair[u] = v.node_pair[q];
       v.uniq_q[u] = q;
+      v.umulti[u] = v.multi[q];
     }
     carry += total;
   }
@@ -223,6 +224,8 @@ __global__ void k_resid(StepView v) {
       v.rhs[u] = a.hi;
       v.rhs_lo[u] = a.lo;
       v.diag[u] = v.lam + d;
+      v.rowlen[u] = h1 - h0;
+      v.occ_off[q] = 0;
     } else {
       v.part_a[q] = a.hi;
       v.part_c[q] = a.lo;
@@ -252,6 +255,19 @@ __global__ void k_merge_rhs(StepView v, int tag) {
     v.rhs[u] = a.hi;
     v.rhs_lo[u] = a.lo;
     v.diag[u] = v.lam + merge_occ(v, p, tag, v.part_b);
+    int32_t run = 0;
+    for (int32_t t = v.inc_off[p], t1 = v.inc_off[p + 1]; t < t1; ++t) {
+      const int32_t bb = v.inc_b[t];
+      if (v.blk_stamp[bb] != tag) continue;
+      const int32_t qq = v.inc_q[t];
+      const int32_t qb1 = v.blk_node_off[bb + 1];
+      const int64_t e0 = (int64_t)bb * v.B;
+      const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
+      const int h1 = (qq + 1 < qb1) ? (int)v.node_he[qq + 1] : 2 * ne;
+      v.occ_off[qq] = run;
+      run += h1 - (int)v.node_he[qq];
+    }
+    v.rowlen[u] = run;
   }
 }
 
@@ -278,15 +294,18 @@ __device__ bool grid_barrier(int32_t* counters) {
       __threadfence();
       atomicAdd(&counters[kCntBarGen], 1);
     } else {
-      const uint64_t t0 = gtimer();
-      while (*gen == g0) {
-        if (((volatile int32_t*)counters)[kCntError] != 0) { ok = 0; break; }
-        if (gtimer() - t0 > 2000000000ull) {
-          set_error(counters, SPIDER_E_TIMEOUT);
-          ok = 0;
-          break;
+      uint64_t t0 = 0;
+      for (uint32_t n = 1; *gen == g0; ++n) {
+        if ((n & 1023u) == 0) {
+          if (((volatile int32_t*)counters)[kCntError] != 0) { ok = 0; break; }
+          const uint64_t t = gtimer();
+          if (t0 == 0) t0 = t;
+          else if (t - t0 > 2000000000ull) {
+            set_error(counters, SPIDER_E_TIMEOUT);
+            ok = 0;
+            break;
+          }
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -319,72 +338,67 @@ __device__ __forceinline__ BlockRange block_range(const StepView& v, int64_t s) 
   return r;
 }
 
-// Ap = lambda p + B^T B p (FP32): node sums over each selected block's half-edges,
-// single nodes written directly, shared nodes as per-occurrence partials.
-__device__ void matvec_f32(const StepView& v, int64_t n_b, const float* __restrict__ p, float* pl) {
-  for (int64_t s = blockIdx.x; s < n_b; s += gridDim.x) {
-    const BlockRange br = block_range(v, s);
-    __syncthreads();
-    for (int l = threadIdx.x; l < br.L; l += blockDim.x) pl[l] = p[v.loc2u[br.q0 + l]];
-    __syncthreads();
-    const uint16_t* he = v.blk_he + 2 * br.e0;
-    for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
-      const int32_t q = br.q0 + l;
-      const int h0 = v.node_he[q];
-      const int h1 = (l + 1 < br.L) ? (int)v.node_he[q + 1] : 2 * br.ne;
-      const float pself = pl[l];
-      float acc = 0.f;
-      for (int h = h0; h < h1; ++h) {
-        const int code = he[h];
-        const int e = code >> 1;
-        const uint32_t lij = v.obs_l[br.e0 + e];
-        const int other = (code & 1) ? (int)(lij & 0xFFFF) : (int)(lij >> 16);
-        const float w = v.obs_sw[br.e0 + e];
-        acc += (w * w) * (pself - pl[other]);
-      }
-      if (!v.multi[q]) v.Ap[v.loc2u[q]] = v.lam * pself + acc;
-      else v.part_a[q] = acc;
-    }
-  }
+// ---- CSR of the merged minibatch matrix: row u = unique pair, entries in
+// block order then half-edge order (so every sum below has a fixed order).
+// Three-phase exclusive scan of rowlen over [0, P_u) into rowptr.
+__global__ void k_scan_rows_a(StepView v) {
+  __shared__ int sm[33];
+  const int64_t P_u = v.counters[kCntPairs];
+  const int64_t chunk = (P_u + gridDim.x - 1) / gridDim.x;
+  const int64_t a = blockIdx.x * chunk, b = a + chunk < P_u ? a + chunk : P_u;
+  int acc = 0;
+  for (int64_t u = a + threadIdx.x; u < b; u += blockDim.x) acc += v.rowlen[u];
+  acc = block_sum<int>(acc, sm);
+  if (threadIdx.x == 0) v.scan_part[blockIdx.x] = acc;
 }
 
-// rres = u - (lambda I + B^T B) z, evaluated in double-float from z = z_hi + z_lo
-// (the residual of iterative refinement), rounded to FP32.
-__device__ void residual_df(const StepView& v, int64_t n_b, float* zh, float* zl) {
-  for (int64_t s = blockIdx.x; s < n_b; s += gridDim.x) {
-    const BlockRange br = block_range(v, s);
-    __syncthreads();
-    for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
-      const int32_t u = v.loc2u[br.q0 + l];
-      zh[l] = v.z[u];
-      zl[l] = v.z_lo[u];
-    }
-    __syncthreads();
-    const uint16_t* he = v.blk_he + 2 * br.e0;
-    for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
-      const int32_t q = br.q0 + l;
-      const int h0 = v.node_he[q];
-      const int h1 = (l + 1 < br.L) ? (int)v.node_he[q + 1] : 2 * br.ne;
-      const df32 zs = {zh[l], zl[l]};
-      df32 acc = {0.f, 0.f};
-      for (int h = h0; h < h1; ++h) {
-        const int code = he[h];
-        const int e = code >> 1;
-        const uint32_t lij = v.obs_l[br.e0 + e];
-        const int o = (code & 1) ? (int)(lij & 0xFFFF) : (int)(lij >> 16);
-        const float sw = v.obs_sw[br.e0 + e];
-        const df32 d = df_add(zs, df32{-zh[o], -zl[o]});
-        acc = df_add(acc, df_mul(df_two_prod(sw, sw), d));
-      }
-      if (!v.multi[q]) {
-        const int32_t u = v.loc2u[q];
-        df32 r = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zs, -v.lam));
-        r = df_add(r, df32{-acc.hi, -acc.lo});
-        v.rres[u] = r.hi;
-      } else {
-        v.part_a[q] = acc.hi;
-        v.part_c[q] = acc.lo;
-      }
+__global__ void k_scan_rows_b(StepView v, int parts) {
+  __shared__ int sm[33];
+  int carry = 0;
+  for (int c = 0; c < parts; c += blockDim.x) {
+    const int i = c + threadIdx.x;
+    const int val = i < parts ? v.scan_part[i] : 0;
+    int total;
+    const int pre = block_exscan(val, sm, &total);
+    if (i < parts) v.scan_part[i] = carry + pre;
+    carry += total;
+  }
+  if (threadIdx.x == 0) v.scan_part[parts] = carry;
+}
+
+__global__ void k_scan_rows_c(StepView v) {
+  __shared__ int sm[33];
+  const int64_t P_u = v.counters[kCntPairs];
+  const int64_t chunk = (P_u + gridDim.x - 1) / gridDim.x;
+  const int64_t a = blockIdx.x * chunk, b = a + chunk < P_u ? a + chunk : P_u;
+  int carry = v.scan_part[blockIdx.x];
+  for (int64_t c = a; c < b; c += blockDim.x) {
+    const int64_t u = c + threadIdx.x;
+    const int val = u < b ? v.rowlen[u] : 0;
+    int total;
+    const int pre = block_exscan(val, sm, &total);
+    if (u < b) v.rowptr[u] = carry + pre;
+    carry += total;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) v.rowptr[P_u] = v.scan_part[gridDim.x];
+}
+
+// entries of every occurrence: neighbour's unique index and sqrt(w_e)
+__global__ void k_fill_rows(StepView v) {
+  const BlockRange br = block_range(v, blockIdx.x);
+  const uint16_t* he = v.blk_he + 2 * br.e0;
+  for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
+    const int32_t q = br.q0 + l;
+    const int h0 = v.node_he[q];
+    const int h1 = (l + 1 < br.L) ? (int)v.node_he[q + 1] : 2 * br.ne;
+    const int32_t base = v.rowptr[v.loc2u[q]] + v.occ_off[q] - h0;
+    for (int h = h0; h < h1; ++h) {
+      const int code = he[h];
+      const int e = code >> 1;
+      const uint32_t lij = v.obs_l[br.e0 + e];
+      const int other = (code & 1) ? (int)(lij & 0xFFFF) : (int)(lij >> 16);
+      v.csr_col[base + h] = v.loc2u[br.q0 + other];
+      v.csr_sw[base + h] = v.obs_sw[br.e0 + e];
     }
   }
 }
@@ -393,14 +407,16 @@ __device__ void residual_df(const StepView& v, int64_t n_b, float* zh, float* zl
 // different groups never share an edge) by iterative refinement: the residual
 // is evaluated in double-float, each correction by Jacobi-preconditioned FP32 CG
 // to a relative tolerance of 1e-3; stop when |u - A z| <= tol |u| (double-float
-// residual) or after max_it inner iterations in total.
-__global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n_b, int max_it, float tol) {
-  extern __shared__ float pl[];
+// residual) or after max_it inner iterations in total.  The CG recurs
+// A p = A y + beta A p so that its SpMV runs on y, which is complete after the
+// update phase: two grid barriers per iteration.
+__global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) {
   __shared__ float smr[33];
   const int G = gridDim.x;
   const int32_t P_u = v.counters[kCntPairs];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = G * blockDim.x;
   float* red = v.red;
+  const float lam = v.lam;
   constexpr float kInnerTol = 1e-3f;
   constexpr int kMaxRounds = 8;
   float bb = 0.f;
@@ -417,31 +433,30 @@ __global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n
   const float outer_thr = tol * tol * bb;
   int it = 0;
   for (int round = 0; round < kMaxRounds && bb > 0.f && it < max_it; ++round) {
-    // outer residual in double-float
-    if (round == 0) {
-      for (int32_t u = gtid; u < P_u; u += gstride) v.rres[u] = v.rhs[u] + v.rhs_lo[u];
-    } else {
-      residual_df(v, n_b, pl, pl + v.L_max);
-      if (!grid_barrier(v.counters)) return;
-      for (int32_t u = gtid; u < P_u; u += gstride) {
-        const int32_t q = v.uniq_q[u];
-        if (!v.multi[q]) continue;
-        const df32 acc = merge_occ_df(v, v.node_pair[q], tag);
-        df32 r = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(df32{v.z[u], v.z_lo[u]}, -v.lam));
-        r = df_add(r, df32{-acc.hi, -acc.lo});
-        v.rres[u] = r.hi;
-      }
-    }
-    // inner PCG on A dz = rres
+    // outer residual u - A z in double-float; inner start: res = y = D^-1 res
     float rz = 0.f, rr0 = 0.f;
     for (int32_t u = gtid; u < P_u; u += gstride) {
-      const float r = v.rres[u];
+      float r;
+      if (round == 0) {
+        r = v.rhs[u] + v.rhs_lo[u];
+      } else {
+        const df32 zu = {v.z[u], v.z_lo[u]};
+        df32 acc = {0.f, 0.f};
+        for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
+          const int32_t c = v.csr_col[t];
+          const float sw = v.csr_sw[t];
+          acc = df_add(acc, df_mul(df_two_prod(sw, sw), df_add(zu, df32{-v.z[c], -v.z_lo[c]})));
+        }
+        df32 rd = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zu, -lam));
+        rd = df_add(rd, df32{-acc.hi, -acc.lo});
+        r = rd.hi;
+      }
       const float y = r / v.diag[u];
-      v.dz[u] = 0.f;
       v.res[u] = r;
-      v.pv[u] = y;
-      rz += r * y;
-      rr0 += r * r;
+      v.yv[u] = y;
+      v.dz[u] = 0.f;
+      rz = fmaf(r, y, rz);
+      rr0 = fmaf(r, r, rr0);
     }
     rz = block_sum<float>(rz, smr);
     rr0 = block_sum<float>(rr0, smr);
@@ -452,37 +467,41 @@ __global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n
     if (!grid_barrier(v.counters)) return;
     rz = sum_partials(red + 0 * kMaxGrid, G, smr);
     rr0 = sum_partials(red + 1 * kMaxGrid, G, smr);
-    if (rr0 <= outer_thr) break;                       // refined solution is accurate enough
+    if (rr0 <= outer_thr) break;                 // refined solution is accurate enough
     const float inner_thr = kInnerTol * kInnerTol * rr0;
+    float beta = 0.f;
+    bool first = true;
     while (it < max_it) {
-      matvec_f32(v, n_b, v.pv, pl);
-      if (!grid_barrier(v.counters)) return;
-      float pap = 0.f;
+      // p = y + beta p;  A p = A y + beta A p;  p.Ap
+      float dot = 0.f;
       for (int32_t u = gtid; u < P_u; u += gstride) {
-        const int32_t q = v.uniq_q[u];
-        float ap;
-        if (v.multi[q]) {
-          ap = v.lam * v.pv[u] + merge_occ(v, v.node_pair[q], tag, v.part_a);
-          v.Ap[u] = ap;
-        } else {
-          ap = v.Ap[u];
+        const float yu = v.yv[u];
+        float s = 0.f;
+        for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
+          const float sw = v.csr_sw[t];
+          s = fmaf(sw * sw, yu - v.yv[v.csr_col[t]], s);
         }
-        pap += v.pv[u] * ap;
+        const float ay = fmaf(lam, yu, s);
+        const float pn = first ? yu : fmaf(beta, v.pv[u], yu);
+        const float apn = first ? ay : fmaf(beta, v.Ap[u], ay);
+        v.pv[u] = pn;
+        v.Ap[u] = apn;
+        dot = fmaf(pn, apn, dot);
       }
-      pap = block_sum<float>(pap, smr);
-      if (threadIdx.x == 0) red[2 * kMaxGrid + blockIdx.x] = pap;
+      dot = block_sum<float>(dot, smr);
+      if (threadIdx.x == 0) red[2 * kMaxGrid + blockIdx.x] = dot;
       if (!grid_barrier(v.counters)) return;
-      pap = sum_partials(red + 2 * kMaxGrid, G, smr);
+      const float pap = sum_partials(red + 2 * kMaxGrid, G, smr);
       const float alpha = pap > 0.f ? rz / pap : 0.f;
       float rzn = 0.f, rr = 0.f;
       for (int32_t u = gtid; u < P_u; u += gstride) {
-        v.dz[u] += alpha * v.pv[u];
-        const float r = v.res[u] - alpha * v.Ap[u];
+        v.dz[u] = fmaf(alpha, v.pv[u], v.dz[u]);
+        const float r = fmaf(-alpha, v.Ap[u], v.res[u]);
         v.res[u] = r;
         const float y = r / v.diag[u];
         v.yv[u] = y;
-        rzn += r * y;
-        rr += r * r;
+        rzn = fmaf(r, y, rzn);
+        rr = fmaf(r, r, rr);
       }
       rzn = block_sum<float>(rzn, smr);
       rr = block_sum<float>(rr, smr);
@@ -495,12 +514,11 @@ __global__ void __launch_bounds__(kThreads) k_pcg(StepView v, int tag, int64_t n
       rr = sum_partials(red + 4 * kMaxGrid, G, smr);
       ++it;
       if (rr <= inner_thr || !(pap > 0.f)) break;
-      const float beta = rzn / rz;
+      beta = rzn / rz;
       rz = rzn;
-      for (int32_t u = gtid; u < P_u; u += gstride) v.pv[u] = v.yv[u] + beta * v.pv[u];
-      if (!grid_barrier(v.counters)) return;
+      first = false;
     }
-    // z += dz in double-float
+    // z += dz in double-float; the next round reads z at neighbours
     for (int32_t u = gtid; u < P_u; u += gstride) {
       const df32 zn = df_add_f(df32{v.z[u], v.z_lo[u]}, v.dz[u]);
       v.z[u] = zn.hi;
@@ -731,7 +749,6 @@ cudaError_t launch_select(const StepView& v, int64_t n_b, int full, uint64_t see
 
 size_t resid_smem(const StepView& v) { return (size_t)(3 * v.L_max + 2 * v.B) * sizeof(float); }
 size_t final_smem(const StepView& v) { return (size_t)(2 * v.L_max + v.B) * sizeof(float); }
-size_t pcg_smem(const StepView& v) { return (size_t)2 * v.L_max * sizeof(float); }
 
 cudaError_t configure_step_kernels(const StepView& v) {
   cudaError_t e;
@@ -739,16 +756,15 @@ cudaError_t configure_step_kernels(const StepView& v) {
     return e;
   if ((e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)final_smem(v))))
     return e;
-  if ((e = cudaFuncSetAttribute(k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcg_smem(v))))
-    return e;
   return cudaSuccess;
 }
 
 int pcg_grid(const StepView& v, int num_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, kThreads, pcg_smem(v)) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, 512, 0) != cudaSuccess ||
       per_sm < 1)
     return 0;
+  if (per_sm > 2) per_sm = 2;   // fewer barrier participants; 512 threads each
   int g = num_sms * per_sm;
   return g > kMaxGrid ? kMaxGrid : g;
 }
@@ -762,14 +778,19 @@ cudaError_t launch_resid(const StepView& v, int64_t n_b, int tag, int gu, cudaSt
 cudaError_t launch_pcg(const StepView& v, int tag, int64_t n_b, int max_it, float tol, int grid,
                        cudaStream_t st) {
   if (!v.whiten) return cudaSuccess;
+  (void)tag;
+  const int parts = grid;
+  k_scan_rows_a<<<parts, kThreads, 0, st>>>(v);
+  k_scan_rows_b<<<1, 1024, 0, st>>>(v, parts);
+  k_scan_rows_c<<<parts, kThreads, 0, st>>>(v);
+  k_fill_rows<<<(unsigned)n_b, kThreads, 0, st>>>(v);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   StepView vv = v;
-  int tg = tag;
-  int64_t nb = n_b;
   int mi = max_it;
   float tl = tol;
-  void* args[] = {&vv, &tg, &nb, &mi, &tl};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(kThreads), args,
-                                     pcg_smem(v), st);
+  void* args[] = {&vv, &mi, &tl};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(512), args, 0, st);
 }
 
 cudaError_t launch_finish(const StepView& v, int64_t n_b, int tag, int gu, int mode, float eps,

@@ -105,9 +105,18 @@ struct StepView {
   float* rres;       // outer (double-float) residual rounded to FP32: inner right-hand side
   float* dz;         // inner correction
   float* res;
-  float* pv;
+  float* pv;        // search direction (two buffers, alternating per iteration)
+  float* pv2;
   float* Ap;
   float* yv;
+  uint8_t* umulti;  // per unique pair: 1 if it has occurrences in several selected blocks
+  // merged minibatch matrix lambda I + B^T B as CSR over unique pairs (per solve)
+  int32_t* rowlen;   // [P] half-edges of the pair over all selected occurrences
+  int32_t* rowptr;   // [P + 1]
+  int32_t* occ_off;  // [Q] offset of an occurrence's entries inside its pair's row
+  int32_t* csr_col;  // [2N] neighbour pair (unique index)
+  float* csr_sw;     // [2N] sqrt(w_e) of the edge
+  int32_t* scan_part;  // [kMaxGrid + 1] scan partials
   float* s_u;
   float4* gp;
   int32_t* pstamp;

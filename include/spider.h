@@ -156,7 +156,8 @@ int spider_sync(spider_ctx *ctx);
  * events on the context stream (enable with spider_set_timing(ctx, 1)):
  * out[0] selection+pair table, [1] travel times (the MLP), [2] residuals and
  * whitening, [3] scatter and event reduce + update, [4] whole call.  Also the
- * pairs evaluated (P_u), observations used and whitening iterations. */
+ * pairs evaluated (P_u), observations used and whitening CG iterations (the
+ * largest count of any connected component of the minibatch graph). */
 int spider_set_timing(spider_ctx *ctx, int enable);
 int spider_last_timing(spider_ctx *ctx, float out_ms[5], int64_t *pairs,
                        int64_t *n_obs, int32_t *pcg_iters);

@@ -203,7 +203,7 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
   cudaStream_t st = c->stream;
   if (c->timing) CK(c, cudaEventRecord(c->ev[0], st));
   CK(c, cudaMemsetAsync(v.counters, 0, 3 * sizeof(int32_t), st));
-  CK(c, cudaMemsetAsync(v.counters + kCntBarArrive, 0, 2 * sizeof(int32_t), st));
+  CK(c, cudaMemsetAsync(v.counters + kCntBarArrive, 0, (kCntSlots - kCntBarArrive) * sizeof(int32_t), st));
   CK(c, launch_select(v, n_b, full ? 1 : 0, seed, tag, st));
   if (c->timing) CK(c, cudaEventRecord(c->ev[1], st));
   PairSource src{};
@@ -391,6 +391,17 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   AL(csr_col, 2 * N);
   AL(csr_sw, 2 * N);
   AL(scan_part, kMaxGrid + 1);
+  AL(lab, PP);
+  AL(cslot, PP);
+  AL(ccount, PP);
+  AL(comp_root, PP);
+  AL(comp_off, PP + 1);
+  AL(members, PP + 1);
+  AL(lidx, PP);
+  AL(big, PP);
+  AL(csr_lcol, 2 * N);
+  AL(centries, PP);
+  AL(ctier, PP);
   AL(Ap, PP);
   AL(yv, PP);
   AL(s_u, PP);
@@ -564,7 +575,7 @@ int spider_set_timing(spider_ctx* c, int enable) {
 
 int spider_last_timing(spider_ctx* c, float out_ms[5], int64_t* pairs, int64_t* n_obs, int32_t* pcg_iters) {
   if (!c) return SPIDER_E_INVAL;
-  int32_t cnt[3] = {0, 0, 0};
+  int32_t cnt[kCntSlots] = {0};
   CK(c, cudaMemcpyAsync(cnt, c->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   if (out_ms) {
@@ -576,7 +587,7 @@ int spider_last_timing(spider_ctx* c, float out_ms[5], int64_t* pairs, int64_t* 
   }
   if (pairs) *pairs = cnt[kCntPairs];
   if (n_obs) *n_obs = cnt[kCntObs];
-  if (pcg_iters) *pcg_iters = cnt[kCntIters];
+  if (pcg_iters) *pcg_iters = cnt[kCntIters] > cnt[kCntCompIters] ? cnt[kCntIters] : cnt[kCntCompIters];
   return SPIDER_OK;
 }
 

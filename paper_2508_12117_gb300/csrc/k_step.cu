@@ -340,47 +340,47 @@ __device__ __forceinline__ BlockRange block_range(const StepView& v, int64_t s) 
 
 // ---- CSR of the merged minibatch matrix: row u = unique pair, entries in
 // block order then half-edge order (so every sum below has a fixed order).
-// Three-phase exclusive scan of rowlen over [0, P_u) into rowptr.
-__global__ void k_scan_rows_a(StepView v) {
+// Three-phase exclusive scan of src[0, n) into dst (dst[n] = total), n = *n_dev.
+__global__ void k_scan_a(const int32_t* __restrict__ src, const int32_t* n_dev, int32_t* part) {
   __shared__ int sm[33];
-  const int64_t P_u = v.counters[kCntPairs];
-  const int64_t chunk = (P_u + gridDim.x - 1) / gridDim.x;
-  const int64_t a = blockIdx.x * chunk, b = a + chunk < P_u ? a + chunk : P_u;
+  const int64_t n = *n_dev;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t a = blockIdx.x * chunk, b = a + chunk < n ? a + chunk : n;
   int acc = 0;
-  for (int64_t u = a + threadIdx.x; u < b; u += blockDim.x) acc += v.rowlen[u];
+  for (int64_t u = a + threadIdx.x; u < b; u += blockDim.x) acc += src[u];
   acc = block_sum<int>(acc, sm);
-  if (threadIdx.x == 0) v.scan_part[blockIdx.x] = acc;
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-__global__ void k_scan_rows_b(StepView v, int parts) {
+__global__ void k_scan_b(int32_t* part, int parts) {
   __shared__ int sm[33];
   int carry = 0;
   for (int c = 0; c < parts; c += blockDim.x) {
     const int i = c + threadIdx.x;
-    const int val = i < parts ? v.scan_part[i] : 0;
+    const int val = i < parts ? part[i] : 0;
     int total;
     const int pre = block_exscan(val, sm, &total);
-    if (i < parts) v.scan_part[i] = carry + pre;
+    if (i < parts) part[i] = carry + pre;
     carry += total;
   }
-  if (threadIdx.x == 0) v.scan_part[parts] = carry;
+  if (threadIdx.x == 0) part[parts] = carry;
 }
 
-__global__ void k_scan_rows_c(StepView v) {
+__global__ void k_scan_c(const int32_t* src, const int32_t* n_dev, const int32_t* part, int32_t* dst) {
   __shared__ int sm[33];
-  const int64_t P_u = v.counters[kCntPairs];
-  const int64_t chunk = (P_u + gridDim.x - 1) / gridDim.x;
-  const int64_t a = blockIdx.x * chunk, b = a + chunk < P_u ? a + chunk : P_u;
-  int carry = v.scan_part[blockIdx.x];
+  const int64_t n = *n_dev;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t a = blockIdx.x * chunk, b = a + chunk < n ? a + chunk : n;
+  int carry = part[blockIdx.x];
   for (int64_t c = a; c < b; c += blockDim.x) {
     const int64_t u = c + threadIdx.x;
-    const int val = u < b ? v.rowlen[u] : 0;
+    const int val = u < b ? src[u] : 0;
     int total;
     const int pre = block_exscan(val, sm, &total);
-    if (u < b) v.rowptr[u] = carry + pre;
+    if (u < b) dst[u] = carry + pre;
     carry += total;
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) v.rowptr[P_u] = v.scan_part[gridDim.x];
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) dst[n] = part[gridDim.x];
 }
 
 // entries of every occurrence: neighbour's unique index and sqrt(w_e)
@@ -403,6 +403,433 @@ __global__ void k_fill_rows(StepView v) {
   }
 }
 
+// ---- connected components of the minibatch graph (rows = unique pairs,
+// edges = CSR entries).  Labels converge to the smallest index of each
+// component: roots are only ever hooked below smaller roots (atomicMin), so
+// parent pointers strictly decrease and the fixed point is unique whatever
+// the order of the atomics.  Rounds alternate hooking and full path
+// compression until a round hooks nothing.
+constexpr int kCcRounds = 64;
+constexpr int kCompMax = 256;        // largest component solved by one warp
+constexpr int kCompEnt = 3072;       // largest CSR entry count cached by one warp
+constexpr int kCtaMax = 8192;        // largest component solved by one CTA
+
+__device__ __forceinline__ int32_t cc_root(const int32_t* lab, int32_t u) {
+  const volatile int32_t* vl = lab;
+  int32_t r = u;
+  for (int k = 0; k < 1 << 20; ++k) {
+    const int32_t n = vl[r];
+    if (n == r) return r;
+    r = n;
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(512) k_cc(StepView v) {
+  __shared__ int any;
+  const int32_t P_u = v.counters[kCntPairs];
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+  int32_t* flags = v.scan_part;          // one flag per round
+  for (int32_t u = gtid; u < P_u; u += gstride) {
+    v.lab[u] = u;
+    v.ccount[u] = 0;
+  }
+  for (int i = gtid; i < kCcRounds; i += gstride) flags[i] = 0;
+  if (!grid_barrier(v.counters)) return;
+  int round = 0;
+  for (; round < kCcRounds; ++round) {
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    int changed = 0;
+    for (int32_t u = gtid; u < P_u; u += gstride) {
+      int32_t ru = cc_root(v.lab, u);
+      for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
+        const int32_t rc = cc_root(v.lab, v.csr_col[t]);
+        if (rc == ru) continue;
+        const int32_t lo = rc < ru ? rc : ru, hi = rc < ru ? ru : rc;
+        if (atomicMin(&v.lab[hi], lo) > lo) changed = 1;
+        ru = cc_root(v.lab, u);
+      }
+    }
+    if (changed) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && any) flags[round] = 1;
+    if (!grid_barrier(v.counters)) return;
+    for (int32_t u = gtid; u < P_u; u += gstride) v.lab[u] = cc_root(v.lab, u);
+    if (!grid_barrier(v.counters)) return;
+    if (((volatile int32_t*)flags)[round] == 0) break;
+  }
+  if (round == kCcRounds) {
+    if (gtid == 0) set_error(v.counters, SPIDER_E_TIMEOUT);
+    return;
+  }
+  // member counts per root; root flags for the compaction scan
+  for (int32_t u = gtid; u < P_u; u += gstride) {
+    const int32_t r = v.lab[u];
+    atomicAdd(&v.ccount[r], 1);
+    v.cslot[u] = (r == u) ? 1 : 0;
+  }
+}
+
+// roots (ascending) -> component index; sizes in component order
+__global__ void k_cc_roots(StepView v) {
+  const int32_t P_u = v.counters[kCntPairs];
+  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
+    if (v.lab[u] != u) continue;
+    const int32_t c = v.members[u];          // exclusive scan of root flags (held in members)
+    v.comp_root[c] = u;
+    v.comp_off[c] = v.ccount[u];             // size, scanned in place next
+    v.centries[c] = 0;
+    v.cslot[u] = c;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) v.counters[kCntComps] = v.members[P_u];
+}
+
+// member lists (arbitrary order inside a component; the solver sorts them)
+__global__ void k_cc_fill(StepView v) {
+  const int32_t P_u = v.counters[kCntPairs];
+  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
+    const int32_t r = v.lab[u];
+    const int32_t c = v.cslot[r];
+    const int32_t size = v.comp_off[c + 1] - v.comp_off[c];
+    const int32_t pos = atomicSub(&v.ccount[r], 1) - 1;
+    v.lidx[u] = v.comp_off[c] + pos;          // slot in the member array
+    (void)size;
+    atomicAdd(&v.centries[c], v.rowlen[u]);
+  }
+}
+
+// members into place; solver tier per component: one warp (n <= kCompMax and
+// entries <= kCompEnt), one CTA (n <= kCtaMax), else the grid-wide solver
+__global__ void k_cc_place(StepView v) {
+  const int32_t P_u = v.counters[kCntPairs];
+  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
+    v.members[v.lidx[u]] = u;
+    const int32_t c = v.cslot[v.lab[u]];
+    const int32_t n = v.comp_off[c + 1] - v.comp_off[c];
+    const int tier = (n <= kCompMax && v.centries[c] <= kCompEnt) ? 0 : (n <= kCtaMax ? 1 : 2);
+    v.big[u] = tier == 2 ? 1 : 0;
+    if (u == v.comp_root[c]) v.ctier[c] = (uint8_t)tier;
+  }
+}
+
+__device__ __forceinline__ float warp_allsum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// One warp per component of at most kCompMax nodes and kCompEnt CSR entries:
+// the same iterative refinement as the grid-wide solver (double-float residual,
+// Jacobi-CG corrections to 1e-3) with the component's local CSR and vectors in
+// shared memory.  Members are sorted first so every sum runs in a fixed order.
+constexpr int kCompWarps = 4;
+
+struct WarpSmem {
+  int32_t mu[kCompMax];
+  float vec[8][kCompMax];          // zh, zl, diag, res, y, p, Ap, dz
+  int32_t lrp[kCompMax + 1];
+  uint8_t lcol[kCompEnt];
+  float lsw[kCompEnt];
+};
+
+__device__ void warp_sort(int32_t* a, int n2, int lane) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < n2; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int32_t x = a[i], y = a[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int max_it, float tol) {
+  extern __shared__ __align__(16) uint8_t smem_w[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_w)[w];
+  const int32_t ncomp = v.counters[kCntComps];
+  const float lam = v.lam;
+  int32_t* mu = S.mu;
+  float* zh = S.vec[0];
+  float* zl = S.vec[1];
+  float* dg = S.vec[2];
+  float* rs = S.vec[3];
+  float* yv = S.vec[4];
+  float* pv = S.vec[5];
+  float* ap = S.vec[6];
+  float* dz = S.vec[7];
+  int max_iters = 0;
+  for (int32_t c = blockIdx.x * kCompWarps + w; c < ncomp; c += gridDim.x * kCompWarps) {
+    if (v.ctier[c] != 0) continue;
+    const int32_t off = v.comp_off[c];
+    const int n = v.comp_off[c + 1] - off;
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int i = lane; i < n2; i += 32) mu[i] = i < n ? v.members[off + i] : 0x7FFFFFFF;
+    __syncwarp();
+    warp_sort(mu, n2, lane);
+    for (int i = lane; i < n; i += 32) v.lidx[mu[i]] = i;
+    // local row pointers (warp scan over the sorted members)
+    int carry = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      const int len = i < n ? v.rowlen[mu[i]] : 0;
+      int x = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (i < n) S.lrp[i] = carry + x - len;
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) S.lrp[n] = carry;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const int32_t u = mu[i];
+      const int32_t t0 = v.rowptr[u];
+      const int l0 = S.lrp[i], l1 = S.lrp[i + 1];
+      for (int l = l0; l < l1; ++l) {
+        S.lcol[l] = (uint8_t)v.lidx[v.csr_col[t0 + (l - l0)]];
+        S.lsw[l] = v.csr_sw[t0 + (l - l0)];
+      }
+      zh[i] = 0.f;
+      zl[i] = 0.f;
+      dg[i] = v.diag[u];
+    }
+    __syncwarp();
+    float bb = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const float b = v.rhs[mu[i]];
+      bb = fmaf(b, b, bb);
+    }
+    bb = warp_allsum(bb);
+    const float outer_thr = tol * tol * bb;
+    int it = 0;
+    for (int round = 0; round < 8 && bb > 0.f && it < max_it; ++round) {
+      float rz = 0.f, rr0 = 0.f;
+      for (int i = lane; i < n; i += 32) {
+        const int32_t u = mu[i];
+        float r;
+        if (round == 0) {
+          r = v.rhs[u] + v.rhs_lo[u];
+        } else {
+          const df32 zu = {zh[i], zl[i]};
+          df32 acc = {0.f, 0.f};
+          for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
+            const int lc = S.lcol[l];
+            const float sw = S.lsw[l];
+            acc = df_add(acc, df_mul(df_two_prod(sw, sw), df_add(zu, df32{-zh[lc], -zl[lc]})));
+          }
+          df32 rd = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zu, -lam));
+          rd = df_add(rd, df32{-acc.hi, -acc.lo});
+          r = rd.hi;
+        }
+        const float y = r / dg[i];
+        rs[i] = r;
+        yv[i] = y;
+        dz[i] = 0.f;
+        rz = fmaf(r, y, rz);
+        rr0 = fmaf(r, r, rr0);
+      }
+      rz = warp_allsum(rz);
+      rr0 = warp_allsum(rr0);
+      __syncwarp();
+      if (rr0 <= outer_thr) break;
+      const float inner_thr = 1e-6f * rr0;
+      float beta = 0.f;
+      bool first = true;
+      while (it < max_it) {
+        float dot = 0.f;
+        for (int i = lane; i < n; i += 32) {
+          const float yu = yv[i];
+          float sacc = 0.f;
+          for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
+            const float sw = S.lsw[l];
+            sacc = fmaf(sw * sw, yu - yv[S.lcol[l]], sacc);
+          }
+          const float ay = fmaf(lam, yu, sacc);
+          const float pn = first ? yu : fmaf(beta, pv[i], yu);
+          const float apn = first ? ay : fmaf(beta, ap[i], ay);
+          pv[i] = pn;
+          ap[i] = apn;
+          dot = fmaf(pn, apn, dot);
+        }
+        const float pap = warp_allsum(dot);
+        const float alpha = pap > 0.f ? rz / pap : 0.f;
+        float rzn = 0.f, rr = 0.f;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+          dz[i] = fmaf(alpha, pv[i], dz[i]);
+          const float r = fmaf(-alpha, ap[i], rs[i]);
+          rs[i] = r;
+          const float y = r / dg[i];
+          yv[i] = y;
+          rzn = fmaf(r, y, rzn);
+          rr = fmaf(r, r, rr);
+        }
+        rzn = warp_allsum(rzn);
+        rr = warp_allsum(rr);
+        __syncwarp();
+        ++it;
+        if (rr <= inner_thr || !(pap > 0.f)) break;
+        beta = rzn / rz;
+        rz = rzn;
+        first = false;
+      }
+      for (int i = lane; i < n; i += 32) {
+        const df32 zn = df_add_f(df32{zh[i], zl[i]}, dz[i]);
+        zh[i] = zn.hi;
+        zl[i] = zn.lo;
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) {
+      v.z[mu[i]] = zh[i];
+      v.z_lo[mu[i]] = zl[i];
+    }
+    __syncwarp();
+    if (it > max_iters) max_iters = it;
+  }
+  if (lane == 0 && max_iters > 0) atomicMax(&v.counters[kCntCompIters], max_iters);
+}
+
+// One CTA per component of at most kCtaMax nodes (vectors in global memory,
+// indexed by unique pair; block-level reductions over the sorted members).
+constexpr int kCtaThreads = 512;
+
+__global__ void __launch_bounds__(kCtaThreads) k_comp_solve_cta(StepView v, int max_it, float tol) {
+  __shared__ int32_t mu[kCtaMax];
+  __shared__ float smr[33];
+  const int32_t ncomp = v.counters[kCntComps];
+  const float lam = v.lam;
+  int max_iters = 0;
+  for (int32_t c = blockIdx.x; c < ncomp; c += gridDim.x) {
+    if (v.ctier[c] != 1) continue;
+    const int32_t off = v.comp_off[c];
+    const int n = v.comp_off[c + 1] - off;
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) mu[i] = i < n ? v.members[off + i] : 0x7FFFFFFF;
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+          const int l = i ^ j;
+          if (l > i) {
+            const int32_t x = mu[i], y = mu[l];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              mu[i] = y;
+              mu[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    float bb = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int32_t u = mu[i];
+      const float b = v.rhs[u];
+      v.z[u] = 0.f;
+      v.z_lo[u] = 0.f;
+      bb = fmaf(b, b, bb);
+    }
+    bb = block_sum<float>(bb, smr);
+    const float outer_thr = tol * tol * bb;
+    int it = 0;
+    for (int round = 0; round < 8 && bb > 0.f && it < max_it; ++round) {
+      float rz = 0.f, rr0 = 0.f;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int32_t u = mu[i];
+        float r;
+        if (round == 0) {
+          r = v.rhs[u] + v.rhs_lo[u];
+        } else {
+          const df32 zu = {v.z[u], v.z_lo[u]};
+          df32 acc = {0.f, 0.f};
+          for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
+            const int32_t cc = v.csr_col[t];
+            const float sw = v.csr_sw[t];
+            acc = df_add(acc, df_mul(df_two_prod(sw, sw), df_add(zu, df32{-v.z[cc], -v.z_lo[cc]})));
+          }
+          df32 rd = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zu, -lam));
+          rd = df_add(rd, df32{-acc.hi, -acc.lo});
+          r = rd.hi;
+        }
+        const float y = r / v.diag[u];
+        v.res[u] = r;
+        v.yv[u] = y;
+        v.dz[u] = 0.f;
+        rz = fmaf(r, y, rz);
+        rr0 = fmaf(r, r, rr0);
+      }
+      rz = block_sum<float>(rz, smr);
+      rr0 = block_sum<float>(rr0, smr);
+      if (rr0 <= outer_thr) break;
+      const float inner_thr = 1e-6f * rr0;
+      float beta = 0.f;
+      bool first = true;
+      while (it < max_it) {
+        float dot = 0.f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          const int32_t u = mu[i];
+          const float yu = v.yv[u];
+          float sacc = 0.f;
+          for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
+            const float sw = v.csr_sw[t];
+            sacc = fmaf(sw * sw, yu - v.yv[v.csr_col[t]], sacc);
+          }
+          const float ay = fmaf(lam, yu, sacc);
+          const float pn = first ? yu : fmaf(beta, v.pv[u], yu);
+          const float apn = first ? ay : fmaf(beta, v.Ap[u], ay);
+          v.pv[u] = pn;
+          v.Ap[u] = apn;
+          dot = fmaf(pn, apn, dot);
+        }
+        const float pap = block_sum<float>(dot, smr);
+        const float alpha = pap > 0.f ? rz / pap : 0.f;
+        float rzn = 0.f, rr = 0.f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          const int32_t u = mu[i];
+          v.dz[u] = fmaf(alpha, v.pv[u], v.dz[u]);
+          const float r = fmaf(-alpha, v.Ap[u], v.res[u]);
+          v.res[u] = r;
+          const float y = r / v.diag[u];
+          v.yv[u] = y;
+          rzn = fmaf(r, y, rzn);
+          rr = fmaf(r, r, rr);
+        }
+        rzn = block_sum<float>(rzn, smr);
+        rr = block_sum<float>(rr, smr);
+        ++it;
+        if (rr <= inner_thr || !(pap > 0.f)) break;
+        beta = rzn / rz;
+        rz = rzn;
+        first = false;
+      }
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int32_t u = mu[i];
+        const df32 zn = df_add_f(df32{v.z[u], v.z_lo[u]}, v.dz[u]);
+        v.z[u] = zn.hi;
+        v.z_lo[u] = zn.lo;
+      }
+      __syncthreads();
+    }
+    if (it > max_iters) max_iters = it;
+  }
+  if (threadIdx.x == 0 && max_iters > 0) atomicMax(&v.counters[kCntCompIters], max_iters);
+}
+
 // Solve (lambda I + B^T B) z = u over all station groups at once (nodes of
 // different groups never share an edge) by iterative refinement: the residual
 // is evaluated in double-float, each correction by Jacobi-preconditioned FP32 CG
@@ -419,8 +846,10 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
   const float lam = v.lam;
   constexpr float kInnerTol = 1e-3f;
   constexpr int kMaxRounds = 8;
+  const uint8_t* big = v.big;
   float bb = 0.f;
   for (int32_t u = gtid; u < P_u; u += gstride) {
+    if (!big[u]) continue;
     const float r = v.rhs[u];
     v.z[u] = 0.f;
     v.z_lo[u] = 0.f;
@@ -436,6 +865,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
     // outer residual u - A z in double-float; inner start: res = y = D^-1 res
     float rz = 0.f, rr0 = 0.f;
     for (int32_t u = gtid; u < P_u; u += gstride) {
+      if (!big[u]) continue;
       float r;
       if (round == 0) {
         r = v.rhs[u] + v.rhs_lo[u];
@@ -475,6 +905,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
       // p = y + beta p;  A p = A y + beta A p;  p.Ap
       float dot = 0.f;
       for (int32_t u = gtid; u < P_u; u += gstride) {
+        if (!big[u]) continue;
         const float yu = v.yv[u];
         float s = 0.f;
         for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
@@ -495,6 +926,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
       const float alpha = pap > 0.f ? rz / pap : 0.f;
       float rzn = 0.f, rr = 0.f;
       for (int32_t u = gtid; u < P_u; u += gstride) {
+        if (!big[u]) continue;
         v.dz[u] = fmaf(alpha, v.pv[u], v.dz[u]);
         const float r = fmaf(-alpha, v.Ap[u], v.res[u]);
         v.res[u] = r;
@@ -520,6 +952,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
     }
     // z += dz in double-float; the next round reads z at neighbours
     for (int32_t u = gtid; u < P_u; u += gstride) {
+      if (!big[u]) continue;
       const df32 zn = df_add_f(df32{v.z[u], v.z_lo[u]}, v.dz[u]);
       v.z[u] = zn.hi;
       v.z_lo[u] = zn.lo;
@@ -736,6 +1169,12 @@ __global__ void k_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+#define CK_LAUNCH(call)                      \
+  do {                                       \
+    cudaError_t _e = (call);                 \
+    if (_e != cudaSuccess) return _e;        \
+  } while (0)
+
 static inline int grid_for(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
 cudaError_t launch_select(const StepView& v, int64_t n_b, int full, uint64_t seed, int tag, cudaStream_t st) {
@@ -756,16 +1195,22 @@ cudaError_t configure_step_kernels(const StepView& v) {
     return e;
   if ((e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)final_smem(v))))
     return e;
+  if ((e = cudaFuncSetAttribute(k_comp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kCompWarps * sizeof(WarpSmem)))))
+    return e;
   return cudaSuccess;
 }
 
 int pcg_grid(const StepView& v, int num_sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, 512, 0) != cudaSuccess ||
-      per_sm < 1)
+  (void)v;
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg, 512, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cc, 512, 0) != cudaSuccess)
     return 0;
+  int per_sm = a < b ? a : b;
   if (per_sm > 2) per_sm = 2;   // fewer barrier participants; 512 threads each
-  int g = num_sms * per_sm;
+  if (per_sm < 1) return 0;
+  const int g = num_sms * per_sm;
   return g > kMaxGrid ? kMaxGrid : g;
 }
 
@@ -779,12 +1224,35 @@ cudaError_t launch_pcg(const StepView& v, int tag, int64_t n_b, int max_it, floa
                        cudaStream_t st) {
   if (!v.whiten) return cudaSuccess;
   (void)tag;
+  const int32_t* Pdev = v.counters + kCntPairs;
   const int parts = grid;
-  k_scan_rows_a<<<parts, kThreads, 0, st>>>(v);
-  k_scan_rows_b<<<1, 1024, 0, st>>>(v, parts);
-  k_scan_rows_c<<<parts, kThreads, 0, st>>>(v);
+  // CSR of the merged minibatch matrix
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.rowlen, Pdev, v.scan_part);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.rowlen, Pdev, v.scan_part, v.rowptr);
   k_fill_rows<<<(unsigned)n_b, kThreads, 0, st>>>(v);
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // connected components
+  {
+    StepView vv = v;
+    void* args[] = {&vv};
+    e = cudaLaunchCooperativeKernel((const void*)k_cc, dim3(grid), dim3(512), args, 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  CK_LAUNCH(cudaMemsetAsync(v.counters + kCntBarArrive, 0, 2 * sizeof(int32_t), st));
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.cslot, Pdev, v.scan_part);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.cslot, Pdev, v.scan_part, v.members);
+  k_cc_roots<<<parts, kThreads, 0, st>>>(v);
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part, v.comp_off);
+  k_cc_fill<<<parts, kThreads, 0, st>>>(v);
+  k_cc_place<<<parts, kThreads, 0, st>>>(v);
+  k_comp_solve<<<2 * parts, kCompWarps * 32, kCompWarps * sizeof(WarpSmem), st>>>(v, max_it, tol);
+  k_comp_solve_cta<<<parts, kCtaThreads, 0, st>>>(v, max_it, tol);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   StepView vv = v;
   int mi = max_it;

@@ -13,6 +13,8 @@ enum : int {
   kCntError = 3,     // first device-side error (SPIDER_E_*), sticky until read
   kCntBarArrive = 4, // grid barrier arrivals
   kCntBarGen = 5,    // grid barrier generation
+  kCntComps = 6,     // connected components of the minibatch graph
+  kCntCompIters = 7, // largest CG iteration count of a component solved by one warp
   kCntSlots = 8
 };
 
@@ -117,6 +119,18 @@ struct StepView {
   int32_t* csr_col;  // [2N] neighbour pair (unique index)
   float* csr_sw;     // [2N] sqrt(w_e) of the edge
   int32_t* scan_part;  // [kMaxGrid + 1] scan partials
+  // connected components of the minibatch graph (per solve)
+  int32_t* lab;      // [P] component label = smallest unique index in the component
+  int32_t* cslot;    // [P] per root: component index; per member: position (scratch)
+  int32_t* ccount;   // [P] member count per root
+  int32_t* comp_root;  // [P] roots in ascending order
+  int32_t* comp_off;   // [P + 1] member list offsets
+  int32_t* members;    // [P] member lists (sorted within each component by the solver)
+  int32_t* lidx;       // [P] local index of a member inside its component
+  uint8_t* big;        // [P] 1: the row belongs to a component solved by the grid-wide CG
+  int16_t* csr_lcol;   // [2N] neighbour's local index inside its component
+  int32_t* centries;   // [P] CSR entries per component
+  uint8_t* ctier;      // [P] per component: 0 one warp, 1 one CTA, 2 grid-wide
   float* s_u;
   float4* gp;
   int32_t* pstamp;

@@ -125,6 +125,21 @@ int spider_create(const spider_catalog *cat, const spider_stations *sta,
                   const spider_net *net, const spider_config *cfg, void *stream,
                   spider_ctx **out);
 
+/* Many independent samplers in one context: n_catalogs catalogs (each with its
+ * own stations) times `chains` chains each (Sec. 3.5 runs one chain per GPU;
+ * here every chain of every catalog advances in the same kernel launches, and
+ * spider_sgld_step relaunches one captured CUDA graph per step).  Sub-problem
+ * s = catalog c * chains + h keeps its own events, minibatch, N/n scale,
+ * centroid prior and Langevin noise: its blocks are drawn with the key
+ * batch_seed XOR (s * 0x9E3779B97F4A7C15) and its noise uses counter
+ * (event index in catalog c, h, c, 'NOIS') with key batch_seed (cfg->chain and
+ * cfg->catalog are ignored).  States, gradients and samples are laid out
+ * sub-problem by sub-problem: [c][h][event][4].  Inputs are copied. */
+int spider_create_batch(int32_t n_catalogs, const spider_catalog *cats,
+                        const spider_stations *stas, const spider_net *net,
+                        const spider_config *cfg, int32_t chains, void *stream,
+                        spider_ctx **out);
+
 /* Gradient of the log posterior at the current state (Eq. sgd without the
  * step): minibatch keyed by batch_seed (0 = full batch), likelihood scaled by
  * N/n.  grad_out: host M x 4 FP32 (caller order) or NULL.  logpost_out: host
@@ -135,7 +150,8 @@ int spider_grad_logpost(spider_ctx *ctx, uint64_t batch_seed, float *grad_out,
 /* One SGLD step (Sec. 3.2): minibatch and Langevin noise both keyed by
  * batch_seed; theta += eps * grad + noise_scale * sqrt(2 eps) * eta.  Asynchronous
  * on the context stream; errors found on the device surface at the next
- * synchronous call. */
+ * synchronous call.  While timing is off the step's kernels run as one CUDA
+ * graph, captured on the first call (make it outside any other capture). */
 int spider_sgld_step(spider_ctx *ctx, float eps, uint64_t batch_seed);
 
 /* Copies up to `cap` stored samples (oldest first) as M x 4 FP64 each, caller
@@ -169,6 +185,28 @@ int spider_last_timing(spider_ctx *ctx, float out_ms[5], int64_t *pairs,
 int spider_debug_blocks(spider_ctx *ctx, int64_t *out, int64_t cap, int64_t *n);
 int spider_debug_obs(spider_ctx *ctx, int64_t *idx_out, float *r_out, float *q_out,
                      int64_t cap, int64_t *n);
+
+/* Launch-shape knobs that change speed but not results (every pair and every
+ * connected component is computed independently of how work is spread):
+ * knobs[0] CTAs per SM-slot of the per-component warp solver (1..8),
+ * knobs[1] of the per-component CTA solver (1..4), knobs[2] CTAs per SM of
+ * the FP32 MLP kernel (1..2).  Invalidates the captured step graph. */
+int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
+
+/* Facts about a context (synchronous), out[0..n): [0] sub-problems,
+ * [1] 1 if the SGLD step runs as a captured CUDA graph, [2] blocks per
+ * minibatch step, [3] blocks in total, [4] pairs in total, [5] events,
+ * [6] observations, [7] connected components of the last minibatch graph. */
+int spider_info(spider_ctx *ctx, int64_t *out, int32_t n);
+
+/* Sampler diagnostics of Sec. 3.6 at the current state, accumulated in FP64 on
+ * the device: the minibatch gradient g (batch_seed) and the full-batch
+ * gradient G are evaluated; grad_norms_out (host, M, caller order, or NULL)
+ * receives |g_m|; *ratio_out receives the variance of the stochastic gradient
+ * relative to the injected Langevin noise, eps^2 mean((g - G)^2) / (2 eps),
+ * the quantity the paper tunes eps against (0.1-1). */
+int spider_diagnostics(spider_ctx *ctx, uint64_t batch_seed, float eps, double *grad_norms_out,
+                       double *ratio_out);
 
 const char *spider_last_error(const spider_ctx *ctx);
 void spider_destroy(spider_ctx *ctx);

@@ -1,0 +1,80 @@
+"""Launch-shape autotuner.
+
+Times every candidate setting of the knobs of `spider_set_tuning` (warp- and
+CTA-solver grid multipliers, FP32 MLP CTAs per SM) on a live context for a few
+SGLD steps, keeps the fastest, and caches it per workload signature in a JSON
+file (SPIDER_TUNE_CACHE, default ~/.cache/spider_gb300/tuning.json).  The knobs
+change speed only: results are identical for every setting.  The chain state is
+restored afterwards, so tuning does not advance the sampler."""
+from __future__ import annotations
+
+import json
+import os
+import time
+from typing import Dict, Optional, Tuple
+
+from .binding import FP32, Context
+
+CACHE = os.environ.get("SPIDER_TUNE_CACHE",
+                       os.path.join(os.path.expanduser("~"), ".cache", "spider_gb300", "tuning.json"))
+
+
+def candidates(precision: int):
+    mlp = (1, 2) if precision == FP32 else (2,)
+    return [(w, c, f) for w in (1, 2, 4) for c in (1, 2) for f in mlp]
+
+
+def signature(ctx: Context, precision: int, hidden: int) -> str:
+    try:
+        import torch
+        gpu = torch.cuda.get_device_name().replace(" ", "_")
+    except Exception:
+        gpu = "gpu"
+    i = ctx.spider_info()
+    return (f"{gpu}/sub{i['n_sub']}/ev{i['events']}/obs{i['obs']}/blk{i['blocks_per_step']}"
+            f"/p{precision}/H{hidden}")
+
+
+def _load(path: str) -> Dict[str, list]:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def autotune(ctx: Context, eps: float, precision: int, hidden: int, steps: int = 4,
+             seed0: int = 0x5EED, path: Optional[str] = None,
+             use_cache: bool = True) -> Tuple[tuple, Dict[str, float]]:
+    path = path or CACHE
+    key = signature(ctx, precision, hidden)
+    cache = _load(path)
+    if use_cache and key in cache:
+        knobs = tuple(cache[key])
+        ctx.spider_set_tuning(knobs)
+        return knobs, {}
+    theta, step = ctx.spider_get_state()
+    timings: Dict[str, float] = {}
+    best = None
+    for knobs in candidates(precision):
+        ctx.spider_set_tuning(knobs)
+        ctx.spider_sgld_step(eps, seed0)          # captures the step graph for this shape
+        ctx.spider_sync()
+        t = time.perf_counter()
+        for s in range(steps):
+            ctx.spider_sgld_step(eps, seed0 + 1 + s)
+        ctx.spider_sync()
+        dt = (time.perf_counter() - t) / steps
+        timings[str(knobs)] = dt
+        if best is None or dt < best[1]:
+            best = (knobs, dt)
+    ctx.spider_set_tuning(best[0])
+    ctx.spider_set_state(theta, step)
+    cache[key] = list(best[0])
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    except OSError:
+        pass
+    return best[0], timings

@@ -70,6 +70,9 @@ def load_library(path: str = LIB_PATH):
         "spider_config_default": (None, [C.POINTER(spider_config)]),
         "spider_create": (C.c_int, [C.POINTER(spider_catalog), C.POINTER(spider_stations),
                                     C.POINTER(spider_net), C.POINTER(spider_config), vp, C.POINTER(vp)]),
+        "spider_create_batch": (C.c_int, [i32, C.POINTER(spider_catalog), C.POINTER(spider_stations),
+                                          C.POINTER(spider_net), C.POINTER(spider_config), i32, vp,
+                                          C.POINTER(vp)]),
         "spider_grad_logpost": (C.c_int, [vp, u64, pf, pd]),
         "spider_sgld_step": (C.c_int, [vp, f32, u64]),
         "spider_samples": (C.c_int, [vp, pd, i64, pi64]),
@@ -81,6 +84,9 @@ def load_library(path: str = LIB_PATH):
         "spider_debug_blocks": (C.c_int, [vp, pi64, i64, pi64]),
         "spider_debug_obs": (C.c_int, [vp, pi64, pf, pf, i64, pi64]),
         "spider_last_error": (C.c_char_p, [vp]),
+        "spider_info": (C.c_int, [vp, pi64, i32]),
+        "spider_set_tuning": (C.c_int, [vp, C.POINTER(i32), i32]),
+        "spider_diagnostics": (C.c_int, [vp, u64, f32, pd, pd]),
         "spider_destroy": (None, [vp]),
         "spider_net_upload": (C.c_int, [C.POINTER(spider_net), i32, C.POINTER(vp)]),
         "spider_net_free": (None, [vp]),
@@ -197,6 +203,35 @@ class Context:
         self._arrays = None
 
     @classmethod
+    def batch(cls, cats, chains: int, net: Net, cfg: spider_config, stream: Optional[int] = None):
+        """spider_create_batch over synthetic catalogs (list), `chains` chains each."""
+        self = cls.__new__(cls)
+        L = load_library()
+        keep = []
+        ccats = (spider_catalog * len(cats))()
+        cstas = (spider_stations * len(cats))()
+        for a, cat in enumerate(cats):
+            arr = [np.ascontiguousarray(cat.init_xyzt, dtype=np.float64),
+                   np.ascontiguousarray(cat.i, dtype=np.int32), np.ascontiguousarray(cat.j, dtype=np.int32),
+                   np.ascontiguousarray(cat.k, dtype=np.int32), np.ascontiguousarray(cat.dt, dtype=np.float64),
+                   np.ascontiguousarray(cat.stations, dtype=np.float64)]
+            keep += arr
+            ccats[a] = spider_catalog(cat.M, cat.N, _ptr(arr[0], C.c_double), _ptr(arr[1], C.c_int32),
+                                      _ptr(arr[2], C.c_int32), _ptr(arr[3], C.c_int32),
+                                      _ptr(arr[4], C.c_double), None)
+            cstas[a] = spider_stations(cat.S, _ptr(arr[5], C.c_double))
+        h = C.c_void_p()
+        _check(L.spider_create_batch(len(cats), ccats, cstas, C.byref(net.s), C.byref(cfg), chains,
+                                     C.c_void_p(stream) if stream else None, C.byref(h)), None)
+        self.h = h
+        self.net = net
+        self.cfg = cfg
+        self.M = sum(c.M for c in cats) * chains
+        self.N = sum(c.N for c in cats) * chains
+        self._arrays = None
+        return self
+
+    @classmethod
     def from_catalog(cls, cat, net: Optional[Net] = None, **cfg_over):
         cfg = config_for_catalog(cat, **cfg_over)
         return cls(cat.init_xyzt, cat.i, cat.j, cat.k, cat.dt, cat.stations,
@@ -253,6 +288,23 @@ class Context:
         _check(load_library().spider_last_timing(self.h, ms, C.byref(pairs), C.byref(nobs),
                                                  C.byref(it)), self.h)
         return dict(ms=list(ms), pairs=pairs.value, n_obs=nobs.value, pcg_iters=it.value)
+
+    def spider_set_tuning(self, knobs):
+        arr = np.ascontiguousarray(knobs, dtype=np.int32)
+        _check(load_library().spider_set_tuning(self.h, _ptr(arr, C.c_int32), arr.size), self.h)
+
+    def spider_info(self):
+        out = np.zeros(8, np.int64)
+        _check(load_library().spider_info(self.h, _ptr(out, C.c_int64), 8), self.h)
+        keys = ["n_sub", "graph", "blocks_per_step", "blocks", "pairs", "events", "obs", "components"]
+        return dict(zip(keys, (int(x) for x in out)))
+
+    def spider_diagnostics(self, batch_seed: int, eps: float):
+        norms = np.empty(self.M, np.float64)
+        ratio = C.c_double()
+        _check(load_library().spider_diagnostics(self.h, C.c_uint64(batch_seed), C.c_float(eps),
+                                                 _ptr(norms, C.c_double), C.byref(ratio)), self.h)
+        return norms, ratio.value
 
     def spider_debug_blocks(self, cap: int = 1 << 20):
         out = np.empty(cap, np.int64)

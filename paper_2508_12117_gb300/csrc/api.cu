@@ -28,8 +28,15 @@ struct spider_ctx {
   float* tt_scratch = nullptr;
   int gu = 0, pgrid = 0;
   int tag = 0;
-  int cur = 0;                     // which centroid partial buffer holds the current state
   int64_t step = 0;
+  int n_sub = 1;
+  int64_t nb_full = 0, nb_mb = 0;  // blocks per step: full batch / minibatch
+  StepParams* prm = nullptr;       // device copy of the per-step parameters
+  cudaGraph_t graph = nullptr;     // the captured SGLD step (timing off)
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_ok = true;
+  bool use_graph = true;
+  int32_t knobs[3] = {2, 1, 2};   // see spider_set_tuning
   int64_t n_samples = 0;           // samples written so far (ring of sample_cap)
   int64_t last_nb = 0;
   bool timing = false;
@@ -192,20 +199,20 @@ int check_device_error(spider_ctx* c) {
   return SPIDER_OK;
 }
 
-// One evaluation of the gradient (mode 0) or one SGLD step (mode 1).
-int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
-  const spider_config& cfg = c->cfg;
+// The kernels of one evaluation, in stream order (everything a step does).
+cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed) {
   StepView& v = c->v;
-  const bool batch_full = cfg.batch_n <= 0 || cfg.batch_n >= v.N;
-  const bool full = batch_full || (mode == 0 && seed == 0);
-  const int64_t n_b = full ? v.NB : std::min<int64_t>(v.NB, (cfg.batch_n + v.B - 1) / v.B);
-  const int tag = ++c->tag;
   cudaStream_t st = c->stream;
-  if (c->timing) CK(c, cudaEventRecord(c->ev[0], st));
-  CK(c, cudaMemsetAsync(v.counters, 0, 3 * sizeof(int32_t), st));
-  CK(c, cudaMemsetAsync(v.counters + kCntBarArrive, 0, (kCntSlots - kCntBarArrive) * sizeof(int32_t), st));
-  CK(c, launch_select(v, n_b, full ? 1 : 0, seed, tag, st));
-  if (c->timing) CK(c, cudaEventRecord(c->ev[1], st));
+  cudaError_t e;
+#define TRY(x)                       \
+  do {                               \
+    if ((e = (x)) != cudaSuccess) return e; \
+  } while (0)
+  TRY(cudaMemsetAsync(v.counters, 0, 3 * sizeof(int32_t), st));
+  TRY(cudaMemsetAsync(v.counters + kCntBarArrive, 0, (kCntSlots - kCntBarArrive) * sizeof(int32_t), st));
+  TRY(cudaMemsetAsync(v.sub_nsel, 0, c->n_sub * sizeof(int32_t), st));
+  TRY(launch_select(v, n_b, st));
+  if (timed) TRY(cudaEventRecord(c->ev[1], st));
   PairSource src{};
   src.uniq_pair = v.uniq_pair;
   src.pair_ev = v.pair_ev;
@@ -218,19 +225,67 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
   src.n_dev = v.counters + kCntPairs;
   src.n_host = v.P;
   TTOut out{v.T2, v.J};
-  CK(c, launch_tt(c->net, src, out, c->num_sms, c->tt_scratch, st));
-  if (c->timing) CK(c, cudaEventRecord(c->ev[2], st));
-  CK(c, launch_resid(v, n_b, tag, c->gu, st));
-  CK(c, launch_pcg(v, tag, n_b, cfg.pcg_max_it, cfg.pcg_tol, c->pgrid, st));
-  if (c->timing) CK(c, cudaEventRecord(c->ev[3], st));
-  int64_t slot = -1;
-  if (mode == 1 && ((c->step + 1) % cfg.thin) == 0 && v.sample_cap > 0) slot = c->n_samples % v.sample_cap;
-  CK(c, launch_finish(v, n_b, tag, c->gu, mode, eps, cfg.noise_scale, seed, c->cur, slot, st));
+  TRY(launch_tt(c->net, src, out, c->num_sms, c->tt_scratch, st, c->knobs[2]));
+  if (timed) TRY(cudaEventRecord(c->ev[2], st));
+  TRY(launch_resid(v, n_b, c->gu, st));
+  TRY(launch_pcg(v, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
+  if (timed) TRY(cudaEventRecord(c->ev[3], st));
+  TRY(launch_finish(v, n_b, c->gu, logpost, st));
+#undef TRY
+  return cudaSuccess;
+}
+
+// One evaluation of the gradient (mode 0) or one SGLD step (mode 1).
+int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
+  const spider_config& cfg = c->cfg;
+  StepView& v = c->v;
+  const bool batch_full = cfg.batch_n <= 0 || cfg.batch_n >= v.N;
+  const bool full = batch_full || (mode == 0 && seed == 0);
+  const int64_t n_b = full ? c->nb_full : c->nb_mb;
+  cudaStream_t st = c->stream;
+  StepParams hp{};
+  hp.seed = seed;
+  hp.eps = eps;
+  hp.noise_scale = cfg.noise_scale;
+  hp.tag = ++c->tag;
+  hp.mode = mode;
+  hp.full = full ? 1 : 0;
+  hp.sample_slot = -1;
+  if (mode == 1 && ((c->step + 1) % cfg.thin) == 0 && v.sample_cap > 0) hp.sample_slot = c->n_samples % v.sample_cap;
+  if (c->timing) CK(c, cudaEventRecord(c->ev[0], st));
+  CK(c, cudaMemcpyAsync(c->prm, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
+  const bool graphable = mode == 1 && !c->timing && c->use_graph && c->graph_ok;
+  if (graphable && !c->graph_exec) {
+    // capture the step once; relaunch it every step with fresh parameters
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e1 = step_sequence(c, n_b, false, false);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+      if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
+          cudaGraphInstantiate(&c->graph_exec, g, 0) == cudaSuccess) {
+        c->graph = g;
+      } else {
+        if (g) cudaGraphDestroy(g);
+        c->graph_exec = nullptr;
+        c->graph_ok = false;
+        cudaGetLastError();   // clear the capture failure; fall back to direct launches
+      }
+    } else {
+      c->graph_ok = false;
+      cudaGetLastError();
+    }
+  }
+  if (graphable && c->graph_exec) {
+    CK(c, cudaGraphLaunch(c->graph_exec, st));
+  } else {
+    const cudaError_t e = step_sequence(c, n_b, mode == 0, c->timing);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+  }
   if (c->timing) CK(c, cudaEventRecord(c->ev[4], st));
   if (mode == 1) {
-    c->cur ^= 1;
     c->step += 1;
-    if (slot >= 0) c->n_samples += 1;
+    if (hp.sample_slot >= 0) c->n_samples += 1;
   }
   c->last_nb = n_b;
   c->have_timing = c->timing;
@@ -266,8 +321,16 @@ void spider_config_default(spider_config* c) {
   c->sample_cap = 16;
 }
 
-int spider_create(const spider_catalog* cat, const spider_stations* sta, const spider_net* net,
-                  const spider_config* cfg, void* stream, spider_ctx** out) {
+}  // extern "C"
+
+namespace {
+
+// Builds a context over a catalog made of n_sub independent sub-problems
+// (a single catalog is one sub-problem); see prepare() for the splits.
+int create_impl(const spider_catalog* cat, const spider_stations* sta, const spider_net* net,
+                const spider_config* cfg, void* stream, spider_ctx** out,
+                const std::vector<int64_t>* ev_splits, const std::vector<int64_t>* obs_splits,
+                const std::vector<int32_t>& sub_chain, const std::vector<int32_t>& sub_catalog) {
   if (!out) return SPIDER_E_INVAL;
   *out = nullptr;
   spider_ctx* c = new spider_ctx();
@@ -291,8 +354,9 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   int rc = check_net(net, cfg->precision, &c->err);
   if (rc) return bail(rc);
   Prep P;
-  rc = prepare(cat, sta, cfg, &P, &c->err);
+  rc = prepare(cat, sta, cfg, &P, &c->err, 0, ev_splits, obs_splits);
   if (rc) return bail(rc);
+  c->n_sub = P.n_sub;
 
   cudaError_t e;
   if ((e = cudaGetDevice(&c->device))) return bail(cuda_fail(c, e, "cudaGetDevice"));
@@ -342,6 +406,55 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   } while (0)
   UP(th0_hi, h_hi.data(), M);
   UP(th0_lo, h_lo.data(), M);
+  UP(ev_caller, P.ev_local.data(), M);
+  {
+    // sub-problem tables
+    const int ns = P.n_sub;
+    std::vector<int32_t> blk_off(ns + 1), sel_full(ns + 1, 0), sel_mb(ns + 1, 0), nobs(ns), nev(ns), ch(ns), ca(ns);
+    std::vector<int32_t> chunk_ev0, sub_chunk_off(ns + 1, 0);
+    const bool bfull = cfg->batch_n <= 0 || cfg->batch_n >= (int64_t)N;
+    for (int s2 = 0; s2 < ns; ++s2) {
+      blk_off[s2] = (int32_t)P.sub_blk_off[s2];
+      const int64_t nbs = P.sub_blk_off[s2 + 1] - P.sub_blk_off[s2];
+      const int64_t want = bfull ? nbs : std::min<int64_t>(nbs, (cfg->batch_n + P.B - 1) / P.B);
+      sel_full[s2 + 1] = sel_full[s2] + (int32_t)nbs;
+      sel_mb[s2 + 1] = sel_mb[s2] + (int32_t)want;
+      nobs[s2] = (int32_t)(P.sub_obs_off[s2 + 1] - P.sub_obs_off[s2]);
+      nev[s2] = (int32_t)(P.sub_ev_off[s2 + 1] - P.sub_ev_off[s2]);
+      ch[s2] = sub_chain[s2];
+      ca[s2] = sub_catalog[s2];
+      sub_chunk_off[s2] = (int32_t)chunk_ev0.size();
+      for (int64_t m = P.sub_ev_off[s2]; m < P.sub_ev_off[s2 + 1]; m += kCenChunk) chunk_ev0.push_back((int32_t)m);
+    }
+    blk_off[ns] = (int32_t)P.sub_blk_off[ns];
+    sub_chunk_off[ns] = (int32_t)chunk_ev0.size();
+    chunk_ev0.push_back((int32_t)M);
+    v.n_sub = ns;
+    v.n_chunks = (int)chunk_ev0.size() - 1;
+    c->nb_full = sel_full[ns];
+    c->nb_mb = sel_mb[ns];
+    UP(blk_e0, P.blk_e0.data(), NB + 1);
+    UP(blk_sub, P.blk_sub.data(), NB);
+    UP(ev_sub, P.ev_sub.data(), M);
+    UP(sub_blk_off, blk_off.data(), ns + 1);
+    UP(sub_sel_full, sel_full.data(), ns + 1);
+    UP(sub_sel_mb, sel_mb.data(), ns + 1);
+    UP(sub_nobs, nobs.data(), ns);
+    UP(sub_nev, nev.data(), ns);
+    UP(sub_chain, ch.data(), ns);
+    UP(sub_catalog, ca.data(), ns);
+    UP(chunk_ev0, chunk_ev0.data(), chunk_ev0.size());
+    UP(sub_chunk_off, sub_chunk_off.data(), ns + 1);
+    AL(sub_nsel, ns);
+    AL(sub_cen, ns);
+    AL(cen_chunk, chunk_ev0.size());
+    StepParams* pp = nullptr;
+    if ((e = dalloc(L, &pp, 1))) return bail(cuda_fail(c, e, "alloc params"));
+    c->prm = pp;
+    v.prm = pp;
+    // the host copies of the tables above must outlive the asynchronous uploads
+    if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "upload sync"));
+  }
   UP(sta_hi, s_hi.data(), S);
   UP(sta_lo, s_lo.data(), S);
   UP(pair_ev, P.pair_ev.data(), PP);
@@ -414,7 +527,6 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   AL(dblk, NB);
   AL(dred, 4 * kMaxGrid);
   AL(dout, 8);
-  AL(cen_part, 2 * kMaxGrid);
   const int64_t cap = c->cfg.sample_cap;
   AL(samples, (size_t)std::max<int64_t>(cap, 1) * M);
 #undef UP
@@ -434,8 +546,6 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   v.inv_sig_c2 = make_float4((float)(1.0 / (cfg->sig_c[0] * cfg->sig_c[0])), (float)(1.0 / (cfg->sig_c[1] * cfg->sig_c[1])),
                              (float)(1.0 / (cfg->sig_c[2] * cfg->sig_c[2])), (float)(1.0 / (cfg->sig_c[3] * cfg->sig_c[3])));
   v.cen_grid = (int)std::min<int64_t>((int64_t)(M + 255) / 256, (int64_t)std::min(kMaxGrid, 4 * c->num_sms));
-  v.chain = (uint32_t)cfg->chain;
-  v.catalog = (uint32_t)cfg->catalog;
   c->gu = std::min(kMaxGrid, 4 * c->num_sms);
 
   if ((e = upload_net(net, cfg->precision, &c->net, L, st))) return bail(cuda_fail(c, e, "network upload"));
@@ -450,7 +560,6 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
     c->err = "whitening kernel does not fit on the device (block too large)";
     return bail(SPIDER_E_UNSUPPORTED);
   }
-  if ((e = launch_cen_init(v, 0, st))) return bail(cuda_fail(c, e, "centroid init"));
   c->ev_old = std::move(P.ev_old);
   c->ord = std::move(P.ord);
   c->th0 = std::move(P.th0);
@@ -459,6 +568,84 @@ int spider_create(const spider_catalog* cat, const spider_stations* sta, const s
   if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "create sync"));
   *out = c;
   return SPIDER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spider_create(const spider_catalog* cat, const spider_stations* sta, const spider_net* net,
+                  const spider_config* cfg, void* stream, spider_ctx** out) {
+  const std::vector<int32_t> ch{cfg ? cfg->chain : 0}, ca{cfg ? cfg->catalog : 0};
+  return create_impl(cat, sta, net, cfg, stream, out, nullptr, nullptr, ch, ca);
+}
+
+int spider_create_batch(int32_t n_catalogs, const spider_catalog* cats, const spider_stations* stas,
+                        const spider_net* net, const spider_config* cfg, int32_t chains, void* stream,
+                        spider_ctx** out) {
+  if (!out) return SPIDER_E_INVAL;
+  *out = nullptr;
+  if (n_catalogs < 1 || chains < 1 || !cats || !stas || !cfg) {
+    g_static_err = "spider_create_batch: need n_catalogs >= 1, chains >= 1 and non-null arrays";
+    return SPIDER_E_INVAL;
+  }
+  // concatenate catalog x chain sub-problems: events and observations copied per
+  // chain, stations once per catalog
+  int64_t M = 0, N = 0, S = 0;
+  bool any_w = false, all_w = true;
+  for (int c = 0; c < n_catalogs; ++c) {
+    if (!cats[c].xyzt0 || !cats[c].i || !cats[c].j || !cats[c].k || !cats[c].dt || !stas[c].xyz ||
+        cats[c].M < 2 || cats[c].N < 1 || stas[c].S < 1) {
+      g_static_err = "spider_create_batch: catalog with null arrays or empty sizes";
+      return SPIDER_E_INVAL;
+    }
+    M += cats[c].M * chains;
+    N += cats[c].N * chains;
+    S += stas[c].S;
+    any_w |= cats[c].w != nullptr;
+    all_w &= cats[c].w != nullptr;
+  }
+  if (any_w != all_w) {
+    g_static_err = "spider_create_batch: give edge weights for every catalog or for none";
+    return SPIDER_E_INVAL;
+  }
+  if (M > INT32_MAX || N >= (int64_t(1) << 30)) {
+    g_static_err = "spider_create_batch: the batch exceeds 2^31 events or 2^30 observations";
+    return SPIDER_E_INVAL;
+  }
+  std::vector<double> xyzt(4 * M), dt(N), sxyz(3 * S);
+  std::vector<int32_t> I(N), J(N), K(N);
+  std::vector<float> W(all_w ? N : 0);
+  std::vector<int64_t> evs{0}, obss{0};
+  std::vector<int32_t> ch, ca;
+  int64_t m0 = 0, n0 = 0, s0 = 0;
+  for (int c = 0; c < n_catalogs; ++c) {
+    const spider_catalog& k = cats[c];
+    std::copy(stas[c].xyz, stas[c].xyz + 3 * stas[c].S, sxyz.begin() + 3 * s0);
+    for (int h = 0; h < chains; ++h) {
+      std::copy(k.xyzt0, k.xyzt0 + 4 * k.M, xyzt.begin() + 4 * m0);
+      for (int64_t n = 0; n < k.N; ++n) {
+        const bool ok = k.i[n] >= 0 && k.i[n] < k.M && k.j[n] >= 0 && k.j[n] < k.M && k.k[n] >= 0 &&
+                        k.k[n] < stas[c].S;
+        // out-of-range indices are kept out of range so that prepare() rejects them
+        I[n0 + n] = ok ? (int32_t)(k.i[n] + m0) : -1;
+        J[n0 + n] = ok ? (int32_t)(k.j[n] + m0) : -1;
+        K[n0 + n] = ok ? (int32_t)(k.k[n] + s0) : -1;
+        dt[n0 + n] = k.dt[n];
+        if (all_w) W[n0 + n] = k.w[n];
+      }
+      m0 += k.M;
+      n0 += k.N;
+      evs.push_back(m0);
+      obss.push_back(n0);
+      ch.push_back(h);
+      ca.push_back(c);
+    }
+    s0 += stas[c].S;
+  }
+  spider_catalog all{M, N, xyzt.data(), I.data(), J.data(), K.data(), dt.data(), all_w ? W.data() : nullptr};
+  spider_stations sall{(int32_t)S, sxyz.data()};
+  return create_impl(&all, &sall, net, cfg, stream, out, &evs, &obss, ch, ca);
 }
 
 int spider_grad_logpost(spider_ctx* c, uint64_t batch_seed, float* grad_out, double* logpost_out) {
@@ -554,8 +741,6 @@ int spider_set_state(spider_ctx* c, const double* theta, int64_t step) {
     buf[m] = make_float4((float)(x[0] - t[0]), (float)(x[1] - t[1]), (float)(x[2] - t[2]), (float)(x[3] - t[3]));
   }
   CK(c, cudaMemcpyAsync(c->v.dth, buf.data(), M * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
-  c->cur = 0;
-  CK(c, launch_cen_init(c->v, 0, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   c->step = step;
   return SPIDER_OK;
@@ -629,6 +814,75 @@ int spider_debug_obs(spider_ctx* c, int64_t* idx_out, float* r_out, float* q_out
   return SPIDER_OK;
 }
 
+int spider_set_tuning(spider_ctx* c, const int32_t* knobs, int32_t n) {
+  if (!c || (n > 0 && !knobs)) return SPIDER_E_INVAL;
+  const int32_t lo[3] = {1, 1, 1}, hi[3] = {8, 4, 2};
+  for (int32_t i = 0; i < n && i < 3; ++i)
+    if (knobs[i] < lo[i] || knobs[i] > hi[i]) {
+      c->err = "tuning knob out of range";
+      return SPIDER_E_INVAL;
+    }
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (int32_t i = 0; i < n && i < 3; ++i) c->knobs[i] = knobs[i];
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  return SPIDER_OK;
+}
+
+int spider_info(spider_ctx* c, int64_t* out, int32_t n) {
+  if (!c || (n > 0 && !out)) return SPIDER_E_INVAL;
+  int32_t cnt[kCntSlots] = {0};
+  CK(c, cudaMemcpyAsync(cnt, c->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int64_t vals[8] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
+                           cnt[kCntComps]};
+  for (int32_t i = 0; i < n && i < 8; ++i) out[i] = vals[i];
+  return SPIDER_OK;
+}
+
+int spider_diagnostics(spider_ctx* c, uint64_t batch_seed, float eps, double* grad_norms_out, double* ratio_out) {
+  if (!c || !(eps > 0.f)) return SPIDER_E_INVAL;
+  const size_t M = c->v.M;
+  float4* gmb = nullptr;
+  double* norms = nullptr;
+  double* part = nullptr;
+  const int grid = std::min(kMaxGrid, 4 * c->num_sms);
+  cudaError_t e = cudaMallocAsync(&gmb, M * sizeof(float4), c->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&norms, M * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&part, grid * sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics buffers");
+  int rc = evaluate(c, batch_seed, 0, 0.f);                 // minibatch gradient
+  if (!rc) {
+    e = cudaMemcpyAsync(gmb, c->v.grad, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "copy");
+  }
+  if (!rc) rc = evaluate(c, 0, 0, 0.f);                      // full-batch gradient
+  std::vector<double> hn(grad_norms_out ? M : 0), hp(grid);
+  if (!rc) {
+    e = launch_diag(c->v, gmb, c->v.grad, norms, part, grid, c->stream);
+    if (e == cudaSuccess && grad_norms_out)
+      e = cudaMemcpyAsync(hn.data(), norms, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, grid * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "diagnostics");
+  }
+  cudaFreeAsync(gmb, c->stream);
+  cudaFreeAsync(norms, c->stream);
+  cudaFreeAsync(part, c->stream);
+  cudaStreamSynchronize(c->stream);
+  if (rc) return rc;
+  rc = check_device_error(c);
+  if (rc) return rc;
+  double ss = 0.0;
+  for (double x : hp) ss += x;
+  if (ratio_out) *ratio_out = (double)eps * eps * (ss / (4.0 * (double)M)) / (2.0 * (double)eps);
+  if (grad_norms_out)
+    for (size_t m = 0; m < M; ++m) grad_norms_out[c->ev_old[m]] = hn[m];
+  return SPIDER_OK;
+}
+
 const char* spider_last_error(const spider_ctx* c) { return c ? c->err.c_str() : g_static_err; }
 
 void spider_destroy(spider_ctx* c) {
@@ -636,6 +890,8 @@ void spider_destroy(spider_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
   free_all(c->allocs);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -694,7 +950,7 @@ int spider_tt_pairs(const spider_netdev* nd, int64_t P, const float* src, const 
   ps.rcv = reinterpret_cast<const float4*>(rcv);
   ps.n_host = P;
   TTOut o{T2, reinterpret_cast<float4*>(J)};
-  e = launch_tt(nd->net, ps, o, nd->num_sms, nd->scratch, st);
+  e = launch_tt(nd->net, ps, o, nd->num_sms, nd->scratch, st, 2);
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(T_hi, sizeof(float), T2, sizeof(float2), sizeof(float), (size_t)P,
                           cudaMemcpyDeviceToDevice, st);

@@ -84,22 +84,37 @@ __device__ __forceinline__ float merge_occ(const StepView& v, int32_t p, int tag
 }
 
 // ------------------------------------------------------------------ selection
-__global__ void k_select(StepView v, int64_t n_b, int full, uint64_t seed, int tag) {
-  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_b) return;
-  int64_t b = full ? s : feistel_index(s, v.NB, seed);
-  if (b < 0 || b >= v.NB) {
-    set_error(v.counters, SPIDER_E_TIMEOUT);
-    b = s % v.NB;
+__global__ void k_select(StepView v, int64_t n_b) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_b) return;
+  const StepParams& pr = *v.prm;
+  const int32_t* so = pr.full ? v.sub_sel_full : v.sub_sel_mb;
+  int lo = 0, hi = v.n_sub;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (so[mid] <= t) lo = mid; else hi = mid;
   }
-  v.sel[s] = (int32_t)b;
-  v.blk_stamp[b] = tag;
-  int64_t sz = (b == v.NB - 1) ? (v.N - (v.NB - 1) * v.B) : v.B;
-  atomicAdd(&v.counters[kCntObs], (int)sz);
+  const int s = lo;
+  const int64_t i = t - so[s];
+  const int64_t nbs = v.sub_blk_off[s + 1] - v.sub_blk_off[s];
+  // each sub-problem draws its blocks with its own key
+  const uint64_t key = pr.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)s);
+  int64_t b = pr.full ? i : feistel_index(i, nbs, key);
+  if (b < 0 || b >= nbs) {
+    set_error(v.counters, SPIDER_E_TIMEOUT);
+    b = i % nbs;
+  }
+  b += v.sub_blk_off[s];
+  v.sel[t] = (int32_t)b;
+  v.blk_stamp[b] = pr.tag;
+  const int sz = v.blk_e0[b + 1] - v.blk_e0[b];
+  atomicAdd(&v.counters[kCntObs], sz);
+  atomicAdd(&v.sub_nsel[s], sz);
 }
 
 // owner of each local node = its occurrence in the selected block of lowest id
-__global__ void k_owner(StepView v, int tag) {
+__global__ void k_owner(StepView v) {
+  const int tag = v.prm->tag;
   __shared__ int sm[33];
   const int s = blockIdx.x;
   const int32_t b = v.sel[s];
@@ -182,8 +197,8 @@ __global__ void k_resid(StepView v) {
   const int32_t b = v.sel[s];
   const int32_t q0 = v.blk_node_off[b];
   const int L = v.blk_node_off[b + 1] - q0;
-  const int64_t e0 = (int64_t)b * v.B;
-  const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
+  const int64_t e0 = v.blk_e0[b];
+  const int ne = v.blk_e0[b + 1] - v.blk_e0[b];
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
     const int32_t q = q0 + l;
     const float2 t = v.T2[v.loc2u[q]];
@@ -245,7 +260,8 @@ __device__ __forceinline__ df32 merge_occ_df(const StepView& v, int32_t p, int t
   return a;
 }
 
-__global__ void k_merge_rhs(StepView v, int tag) {
+__global__ void k_merge_rhs(StepView v) {
+  const int tag = v.prm->tag;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     const int32_t q = v.uniq_q[u];
@@ -261,8 +277,7 @@ __global__ void k_merge_rhs(StepView v, int tag) {
       if (v.blk_stamp[bb] != tag) continue;
       const int32_t qq = v.inc_q[t];
       const int32_t qb1 = v.blk_node_off[bb + 1];
-      const int64_t e0 = (int64_t)bb * v.B;
-      const int ne = (int)(v.N - e0 < v.B ? v.N - e0 : v.B);
+      const int ne = v.blk_e0[bb + 1] - v.blk_e0[bb];
       const int h1 = (qq + 1 < qb1) ? (int)v.node_he[qq + 1] : 2 * ne;
       v.occ_off[qq] = run;
       run += h1 - (int)v.node_he[qq];
@@ -333,8 +348,8 @@ __device__ __forceinline__ BlockRange block_range(const StepView& v, int64_t s) 
   const int32_t b = v.sel[s];
   r.q0 = v.blk_node_off[b];
   r.L = v.blk_node_off[b + 1] - r.q0;
-  r.e0 = (int64_t)b * v.B;
-  r.ne = (int)(v.N - r.e0 < v.B ? v.N - r.e0 : v.B);
+  r.e0 = v.blk_e0[b];
+  r.ne = v.blk_e0[b + 1] - v.blk_e0[b];
   return r;
 }
 
@@ -1014,57 +1029,78 @@ __global__ void k_final(StepView v) {
   }
 }
 
-// s_p * (N/n) times (dT/dx_p, 1) into the global pair slots, stamped.
-__global__ void k_merge_s(StepView v, int tag) {
+// s_p * (N_s/n_s) times (dT/dx_p, 1) into the global pair slots, stamped.
+__global__ void k_merge_s(StepView v) {
+  const int tag = v.prm->tag;
   const int32_t P_u = v.counters[kCntPairs];
-  const float scale = (float)((double)v.N / (double)v.counters[kCntObs]);
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     const int32_t q = v.uniq_q[u];
     const int32_t p = v.node_pair[q];
+    const int32_t m = v.pair_ev[p];
+    const int sb = v.ev_sub[m];
+    const float scale = (float)((double)v.sub_nobs[sb] / (double)v.sub_nsel[sb]);
     float sp = v.multi[q] ? merge_occ(v, p, tag, v.part_a) : v.s_u[u];
     sp *= scale;
     const float4 J = v.J[u];
     v.gp[p] = make_float4(sp * J.x, sp * J.y, sp * J.z, sp);
     v.pstamp[p] = tag;
-    v.estamp[v.pair_ev[p]] = tag;
+    v.estamp[m] = tag;
   }
 }
 
 // ------------------------------------------------------------------ events
-// grad_m = (N/n) sum_k s_(m,k) (dT/dx, 1) - dtheta_m / sigma_e^2
-//          - mean(dtheta) / (M sigma_c^2)             (priors of Sec. 3.1)
-// mode 0: write grad; mode 1: SGLD theta += eps grad + ns sqrt(2 eps) eta (Sec. 3.2)
-__global__ void k_event(StepView v, int tag, int mode, float eps, float noise_scale, uint64_t seed,
-                        int cur, int64_t sample_slot) {
-  __shared__ float4 scen;
+// centroid of the current state offset, per sub-problem: fixed chunks of
+// events summed in a fixed tree, chunks summed in order
+__global__ void k_cen_chunk(StepView v) {
   __shared__ float smr[33];
-  __shared__ double smd[33];
-  const int G = v.cen_grid;
-  // centroid of the current state from the fixed partials of the previous pass
-  if (threadIdx.x < 32) {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = threadIdx.x; i < G; i += 32) {
-      const float4 c = v.cen_part[cur * kMaxGrid + i];
-      a.x += c.x; a.y += c.y; a.z += c.z; a.w += c.w;
-    }
-    a.x = warp_sum(a.x); a.y = warp_sum(a.y); a.z = warp_sum(a.z); a.w = warp_sum(a.w);
-    if (threadIdx.x == 0) {
-      const float invM = 1.0f / (float)v.M;
-      scen = make_float4(a.x * invM, a.y * invM, a.z * invM, a.w * invM);
-    }
+  const int c = blockIdx.x;
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int32_t m = v.chunk_ev0[c] + threadIdx.x; m < v.chunk_ev0[c + 1]; m += blockDim.x) {
+    const float4 d = v.dth[m];
+    a.x += d.x; a.y += d.y; a.z += d.z; a.w += d.w;
   }
-  __syncthreads();
-  const float4 cen = scen;
+  a.x = block_sum<float>(a.x, smr);
+  a.y = block_sum<float>(a.y, smr);
+  a.z = block_sum<float>(a.z, smr);
+  a.w = block_sum<float>(a.w, smr);
+  if (threadIdx.x == 0) v.cen_chunk[c] = a;
+}
+
+__global__ void k_cen_final(StepView v) {
+  __shared__ float smr[33];
+  const int s = blockIdx.x;
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int32_t c = v.sub_chunk_off[s] + threadIdx.x; c < v.sub_chunk_off[s + 1]; c += blockDim.x) {
+    const float4 d = v.cen_chunk[c];
+    a.x += d.x; a.y += d.y; a.z += d.z; a.w += d.w;
+  }
+  a.x = block_sum<float>(a.x, smr);
+  a.y = block_sum<float>(a.y, smr);
+  a.z = block_sum<float>(a.z, smr);
+  a.w = block_sum<float>(a.w, smr);
+  if (threadIdx.x == 0) {
+    const float inv = 1.0f / (float)v.sub_nev[s];
+    v.sub_cen[s] = make_float4(a.x * inv, a.y * inv, a.z * inv, a.w * inv);
+  }
+}
+
+// grad_m = (N_s/n_s) sum_k s_(m,k) (dT/dx, 1) - dtheta_m / sigma_e^2
+//          - mean_s(dtheta) / (M_s sigma_c^2)             (priors of Sec. 3.1)
+// mode 0: write grad; mode 1: SGLD theta += eps grad + ns sqrt(2 eps) eta (Sec. 3.2)
+__global__ void k_event(StepView v) {
+  __shared__ double smd[33];
+  const StepParams& pr = *v.prm;
+  const int tag = pr.tag, mode = pr.mode;
+  const float eps = pr.eps;
   const float4 ise = v.inv_sig_e2, isc = v.inv_sig_c2;
-  const float invM = 1.0f / (float)v.M;
-  const float4 gc = make_float4(cen.x * isc.x * invM, cen.y * isc.y * invM, cen.z * isc.z * invM,
-                                cen.w * isc.w * invM);
-  const float sq = noise_scale * sqrtf(2.0f * eps);
-  const uint2 key = seed_key(seed);
-  float4 csum = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float sq = pr.noise_scale * sqrtf(2.0f * eps);
+  const uint2 key = seed_key(pr.seed);
   double lp = 0.0;
   int bad = 0;
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M; m += (int64_t)G * blockDim.x) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M; m += (int64_t)gridDim.x * blockDim.x) {
+    const int sb = v.ev_sub[m];
+    const float4 cen = v.sub_cen[sb];
+    const float invM = 1.0f / (float)v.sub_nev[sb];
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (v.estamp[m] == tag) {
       for (int32_t p = v.pair_off[m], p1 = v.pair_off[m + 1]; p < p1; ++p)
@@ -1074,18 +1110,19 @@ __global__ void k_event(StepView v, int tag, int mode, float eps, float noise_sc
         }
     }
     const float4 d = v.dth[m];
-    g.x -= d.x * ise.x + gc.x;
-    g.y -= d.y * ise.y + gc.y;
-    g.z -= d.z * ise.z + gc.z;
-    g.w -= d.w * ise.w + gc.w;
+    g.x -= d.x * ise.x + cen.x * isc.x * invM;
+    g.y -= d.y * ise.y + cen.y * isc.y * invM;
+    g.z -= d.z * ise.z + cen.z * isc.z * invM;
+    g.w -= d.w * ise.w + cen.w * isc.w * invM;
     if (mode == 0) {
       v.grad[m] = g;
       lp += (double)d.x * d.x * ise.x + (double)d.y * d.y * ise.y + (double)d.z * d.z * ise.z +
             (double)d.w * d.w * ise.w;
       if (!(isfinite(g.x) && isfinite(g.y) && isfinite(g.z) && isfinite(g.w))) bad = 1;
-      csum.x += d.x; csum.y += d.y; csum.z += d.z; csum.w += d.w;
     } else {
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)m, v.chain, v.catalog, kTagNoise), key);
+      const uint4 w = philox4x32_10(
+          make_uint4((uint32_t)v.ev_caller[m], (uint32_t)v.sub_chain[sb], (uint32_t)v.sub_catalog[sb], kTagNoise),
+          key);
       const float2 n01 = box_muller(w.x, w.y), n23 = box_muller(w.z, w.w);
       float4 nd;
       nd.x = d.x + eps * g.x + sq * n01.x;
@@ -1094,68 +1131,58 @@ __global__ void k_event(StepView v, int tag, int mode, float eps, float noise_sc
       nd.w = d.w + eps * g.w + sq * n23.y;
       if (!(isfinite(nd.x) && isfinite(nd.y) && isfinite(nd.z) && isfinite(nd.w))) bad = 1;
       v.dth[m] = nd;
-      if (sample_slot >= 0) v.samples[sample_slot * v.M + m] = nd;
-      csum.x += nd.x; csum.y += nd.y; csum.z += nd.z; csum.w += nd.w;
+      if (pr.sample_slot >= 0) v.samples[pr.sample_slot * v.M + m] = nd;
     }
   }
   if (bad) set_error(v.counters, SPIDER_E_NONFINITE);
-  csum.x = block_sum<float>(csum.x, smr);
-  csum.y = block_sum<float>(csum.y, smr);
-  csum.z = block_sum<float>(csum.z, smr);
-  csum.w = block_sum<float>(csum.w, smr);
-  if (mode == 1 && threadIdx.x == 0) v.cen_part[(cur ^ 1) * kMaxGrid + blockIdx.x] = csum;
   if (mode == 0) {
     lp = block_sum<double>(lp, smd);
-    if (threadIdx.x == 0) v.dred[2 * kMaxGrid + blockIdx.x] = lp;   // slot 2
+    if (threadIdx.x == 0) v.dred[2 * kMaxGrid + blockIdx.x] = lp;
   }
 }
 
-// centroid partials of the current state (after create / set_state)
-__global__ void k_cen_init(StepView v, int cur) {
-  __shared__ float smr[33];
-  float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M;
-       m += (int64_t)v.cen_grid * blockDim.x) {
-    const float4 d = v.dth[m];
-    c.x += d.x; c.y += d.y; c.z += d.z; c.w += d.w;
-  }
-  c.x = block_sum<float>(c.x, smr);
-  c.y = block_sum<float>(c.y, smr);
-  c.z = block_sum<float>(c.z, smr);
-  c.w = block_sum<float>(c.w, smr);
-  if (threadIdx.x == 0) v.cen_part[cur * kMaxGrid + blockIdx.x] = c;
-}
-
-// FP64 log posterior: -1/2 (N/n) sigma^-2 (r.r - u.z) - 1/2 |dtheta/sigma_e|^2
-//                     - 1/2 |mean(dtheta)/sigma_c|^2   (constants dropped)
-__global__ void k_logpost(StepView v, int64_t n_b, int cur) {
+// FP64 log posterior: sum_s -1/2 (N_s/n_s) r_s^T Sigma^-1 r_s - 1/2 |dtheta/sigma_e|^2
+//                     - 1/2 sum_s |mean_s(dtheta)/sigma_c|^2   (constants dropped)
+__global__ void k_logpost(StepView v, int64_t n_b) {
   __shared__ double smd[33];
   double quad = 0.0, lp = 0.0;
-  for (int64_t i = threadIdx.x; i < n_b; i += blockDim.x) quad += v.dblk[i];
+  for (int64_t t = threadIdx.x; t < n_b; t += blockDim.x) {
+    const int sb = v.blk_sub[v.sel[t]];
+    quad += v.dblk[t] * ((double)v.sub_nobs[sb] / (double)v.sub_nsel[sb]);
+  }
   for (int i = threadIdx.x; i < v.cen_grid; i += blockDim.x) lp += v.dred[2 * kMaxGrid + i];
   quad = block_sum<double>(quad, smd);
   lp = block_sum<double>(lp, smd);
-  double c[4] = {0, 0, 0, 0};
-  for (int i = 0; i < v.cen_grid; ++i) {
-    const float4 p = v.cen_part[cur * kMaxGrid + i];
-    c[0] += p.x; c[1] += p.y; c[2] += p.z; c[3] += p.w;
+  double lc = 0.0;
+  const float isc[4] = {v.inv_sig_c2.x, v.inv_sig_c2.y, v.inv_sig_c2.z, v.inv_sig_c2.w};
+  for (int sb = threadIdx.x; sb < v.n_sub; sb += blockDim.x) {
+    const float4 c = v.sub_cen[sb];
+    const double cc[4] = {c.x, c.y, c.z, c.w};
+    for (int a = 0; a < 4; ++a) lc += cc[a] * cc[a] * (double)isc[a];
   }
+  lc = block_sum<double>(lc, smd);
   if (threadIdx.x == 0) {
-    const double scale = (double)v.N / (double)v.counters[kCntObs];
-    const double ll = -0.5 * scale * quad;
-    const double lpr = -0.5 * lp;
-    const float isc[4] = {v.inv_sig_c2.x, v.inv_sig_c2.y, v.inv_sig_c2.z, v.inv_sig_c2.w};
-    double lc = 0.0;
-    for (int a = 0; a < 4; ++a) {
-      const double mu = c[a] / (double)v.M;
-      lc += mu * mu * (double)isc[a];
-    }
-    lc *= -0.5;
+    const double ll = -0.5 * quad;
     v.dout[0] = ll;
-    v.dout[1] = lpr;
-    v.dout[2] = lc;
-    v.dout[3] = ll + lpr + lc;
+    v.dout[1] = -0.5 * lp;
+    v.dout[2] = -0.5 * lc;
+    v.dout[3] = ll - 0.5 * lp - 0.5 * lc;
   }
+}
+
+// FP64 diagnostics: |g_m| of the minibatch gradient and sum (g - G)^2
+__global__ void k_diag(StepView v, const float4* __restrict__ g, const float4* __restrict__ G,
+                       double* norms, double* part) {
+  __shared__ double smd[33];
+  double acc = 0.0;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M; m += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = g[m], b = G[m];
+    norms[m] = sqrt((double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w);
+    const double dx = (double)a.x - b.x, dy = (double)a.y - b.y, dz = (double)a.z - b.z, dw = (double)a.w - b.w;
+    acc += dx * dx + dy * dy + dz * dz + dw * dw;
+  }
+  acc = block_sum<double>(acc, smd);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
 __global__ void k_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -1177,9 +1204,9 @@ __global__ void k_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t
 
 static inline int grid_for(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
-cudaError_t launch_select(const StepView& v, int64_t n_b, int full, uint64_t seed, int tag, cudaStream_t st) {
-  k_select<<<grid_for(n_b), kThreads, 0, st>>>(v, n_b, full, seed, tag);
-  k_owner<<<(unsigned)n_b, kThreads, 0, st>>>(v, tag);
+cudaError_t launch_select(const StepView& v, int64_t n_b, cudaStream_t st) {
+  k_select<<<grid_for(n_b), kThreads, 0, st>>>(v, n_b);
+  k_owner<<<(unsigned)n_b, kThreads, 0, st>>>(v);
   k_scan_owner<<<1, 1024, 0, st>>>(v, n_b);
   k_assign<<<(unsigned)n_b, kThreads, 0, st>>>(v);
   k_link<<<(unsigned)n_b, kThreads, 0, st>>>(v);
@@ -1214,16 +1241,15 @@ int pcg_grid(const StepView& v, int num_sms) {
   return g > kMaxGrid ? kMaxGrid : g;
 }
 
-cudaError_t launch_resid(const StepView& v, int64_t n_b, int tag, int gu, cudaStream_t st) {
+cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st) {
   k_resid<<<(unsigned)n_b, kThreads, resid_smem(v), st>>>(v);
-  if (v.whiten) k_merge_rhs<<<gu, kThreads, 0, st>>>(v, tag);
+  if (v.whiten) k_merge_rhs<<<gu, kThreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg(const StepView& v, int tag, int64_t n_b, int max_it, float tol, int grid,
-                       cudaStream_t st) {
+cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, int grid, int warp_mult,
+                       int cta_mult, cudaStream_t st) {
   if (!v.whiten) return cudaSuccess;
-  (void)tag;
   const int32_t* Pdev = v.counters + kCntPairs;
   const int parts = grid;
   // CSR of the merged minibatch matrix
@@ -1250,8 +1276,8 @@ cudaError_t launch_pcg(const StepView& v, int tag, int64_t n_b, int max_it, floa
   k_scan_c<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part, v.comp_off);
   k_cc_fill<<<parts, kThreads, 0, st>>>(v);
   k_cc_place<<<parts, kThreads, 0, st>>>(v);
-  k_comp_solve<<<2 * parts, kCompWarps * 32, kCompWarps * sizeof(WarpSmem), st>>>(v, max_it, tol);
-  k_comp_solve_cta<<<parts, kCtaThreads, 0, st>>>(v, max_it, tol);
+  k_comp_solve<<<warp_mult * parts, kCompWarps * 32, kCompWarps * sizeof(WarpSmem), st>>>(v, max_it, tol);
+  k_comp_solve_cta<<<cta_mult * parts, kCtaThreads, 0, st>>>(v, max_it, tol);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   StepView vv = v;
@@ -1261,18 +1287,19 @@ cudaError_t launch_pcg(const StepView& v, int tag, int64_t n_b, int max_it, floa
   return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(512), args, 0, st);
 }
 
-cudaError_t launch_finish(const StepView& v, int64_t n_b, int tag, int gu, int mode, float eps,
-                          float noise_scale, uint64_t seed, int cur, int64_t sample_slot,
-                          cudaStream_t st) {
+cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, cudaStream_t st) {
   k_final<<<(unsigned)n_b, kThreads, final_smem(v), st>>>(v);
-  k_merge_s<<<gu, kThreads, 0, st>>>(v, tag);
-  k_event<<<v.cen_grid, kThreads, 0, st>>>(v, tag, mode, eps, noise_scale, seed, cur, sample_slot);
-  if (mode == 0) k_logpost<<<1, kThreads, 0, st>>>(v, n_b, cur);
+  k_merge_s<<<gu, kThreads, 0, st>>>(v);
+  k_cen_chunk<<<v.n_chunks, kThreads, 0, st>>>(v);
+  k_cen_final<<<v.n_sub, kThreads, 0, st>>>(v);
+  k_event<<<v.cen_grid, kThreads, 0, st>>>(v);
+  if (logpost) k_logpost<<<1, kThreads, 0, st>>>(v, n_b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cen_init(const StepView& v, int cur, cudaStream_t st) {
-  k_cen_init<<<v.cen_grid, kThreads, 0, st>>>(v, cur);
+cudaError_t launch_diag(const StepView& v, const float4* g, const float4* G, double* norms, double* part,
+                        int grid, cudaStream_t st) {
+  k_diag<<<grid, kThreads, 0, st>>>(v, g, G, norms, part);
   return cudaGetLastError();
 }
 

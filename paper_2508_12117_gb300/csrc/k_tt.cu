@@ -270,7 +270,7 @@ size_t tt_scratch_floats(const NetView& net, int num_sms) {
 bool tt_supported_width(int H) { return H == 32 || H == 64 || H == 128 || H == 256; }
 
 cudaError_t launch_tt(const NetView& net, const PairSource& src, TTOut out, int num_sms, float* scratch,
-                      cudaStream_t st) {
+                      cudaStream_t st, int ctas_per_sm) {
   if (net.kind == SPIDER_TT_HOMOGENEOUS) {
     k_tt_homogeneous<<<4 * num_sms, 256, 0, st>>>(net, src, out);
     return cudaGetLastError();
@@ -284,7 +284,7 @@ cudaError_t launch_tt(const NetView& net, const PairSource& src, TTOut out, int 
     if (e != cudaErrorNotSupported) return e;
     return cudaErrorNotSupported;
   }
-  const int grid = mlp_fp32_grid(num_sms);
+  const int grid = (ctas_per_sm == 1 ? 1 : 2) * num_sms;   // never above the scratch slots
   switch (net.H) {
     case 32: return launch_mlp_fp32<32>(net, src, out, grid, scratch, st);
     case 64: return launch_mlp_fp32<64>(net, src, out, grid, scratch, st);

@@ -12,8 +12,9 @@ void set_static_error(const char* msg);
 // travel times (k_tt.cu, k_mlp_tc.cu)
 bool tt_supported_width(int H);
 size_t tt_scratch_floats(const NetView& net, int num_sms);
+// ctas_per_sm (1 or 2) shapes the FP32 MLP grid; scratch holds 2 x num_sms slots
 cudaError_t launch_tt(const NetView& net, const PairSource& src, TTOut out, int num_sms, float* scratch,
-                      cudaStream_t st);
+                      cudaStream_t st, int ctas_per_sm);
 cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms,
                           cudaStream_t st);
 bool mlp_tc_supported(int H, int precision);
@@ -24,14 +25,13 @@ cudaError_t mlp_tc_prepare(const float* const Wn_host[3], int H, int precision, 
 // step (k_step.cu)
 cudaError_t configure_step_kernels(const StepView& v);
 int pcg_grid(const StepView& v, int num_sms);
-cudaError_t launch_select(const StepView& v, int64_t n_b, int full, uint64_t seed, int tag, cudaStream_t st);
-cudaError_t launch_resid(const StepView& v, int64_t n_b, int tag, int gu, cudaStream_t st);
-cudaError_t launch_pcg(const StepView& v, int tag, int64_t n_b, int max_it, float tol, int grid,
-                       cudaStream_t st);
-cudaError_t launch_finish(const StepView& v, int64_t n_b, int tag, int gu, int mode, float eps,
-                          float noise_scale, uint64_t seed, int cur, int64_t sample_slot,
-                          cudaStream_t st);
-cudaError_t launch_cen_init(const StepView& v, int cur, cudaStream_t st);
+cudaError_t launch_select(const StepView& v, int64_t n_b, cudaStream_t st);
+cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st);
+cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, int grid, int warp_mult,
+                       int cta_mult, cudaStream_t st);
+cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, cudaStream_t st);
+cudaError_t launch_diag(const StepView& v, const float4* g, const float4* G, double* norms, double* part,
+                        int grid, cudaStream_t st);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                 int64_t n, uint32_t* out, cudaStream_t st);
 

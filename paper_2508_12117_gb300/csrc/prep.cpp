@@ -68,7 +68,8 @@ std::vector<int32_t> morton_order(const double* xyzt, int64_t M) {
 }
 
 int prepare(const spider_catalog* cat, const spider_stations* sta, const spider_config* cfg,
-            Prep* out, std::string* err, int threads) {
+            Prep* out, std::string* err, int threads, const std::vector<int64_t>* ev_splits,
+            const std::vector<int64_t>* obs_splits) {
   auto fail = [&](const std::string& m) {
     *err = m;
     return SPIDER_E_INVAL;
@@ -91,6 +92,17 @@ int prepare(const spider_catalog* cat, const spider_stations* sta, const spider_
     if (!finite(cat->xyzt0[m])) return fail("non-finite theta_0");
   for (int64_t s = 0; s < 3 * S; ++s)
     if (!finite(sta->xyz[s])) return fail("non-finite station position");
+  std::vector<int64_t> evs = ev_splits ? *ev_splits : std::vector<int64_t>{0, M};
+  std::vector<int64_t> obss = obs_splits ? *obs_splits : std::vector<int64_t>{0, N};
+  const int n_sub = (int)evs.size() - 1;
+  if (n_sub < 1 || (int)obss.size() != n_sub + 1 || evs.front() != 0 || evs.back() != M ||
+      obss.front() != 0 || obss.back() != N)
+    return fail("inconsistent sub-problem splits");
+  for (int s = 0; s < n_sub; ++s)
+    if (evs[s + 1] - evs[s] < 2 || obss[s + 1] < obss[s]) return fail("every sub-problem needs >= 2 events");
+  std::vector<int32_t> obs_sub_of(n_sub > 1 ? N : 0);
+  for (int s = 0; s < n_sub && n_sub > 1; ++s)
+    for (int64_t n = obss[s]; n < obss[s + 1]; ++n) obs_sub_of[n] = s;
   {
     std::atomic<int64_t> bad(-1);
     parallel_for(N, threads, [&](int64_t a, int64_t b) {
@@ -98,6 +110,10 @@ int prepare(const spider_catalog* cat, const spider_stations* sta, const spider_
         int32_t i = cat->i[n], j = cat->j[n], k = cat->k[n];
         bool ok = i >= 0 && i < M && j >= 0 && j < M && i != j && k >= 0 && k < S &&
                   finite(cat->dt[n]) && (!cat->w || (finite(cat->w[n]) && cat->w[n] > 0.f));
+        if (ok && n_sub > 1) {
+          const int s = obs_sub_of[n];
+          ok = i >= evs[s] && i < evs[s + 1] && j >= evs[s] && j < evs[s + 1];
+        }
         if (!ok) {
           int64_t e = -1;
           bad.compare_exchange_strong(e, n);
@@ -112,14 +128,29 @@ int prepare(const spider_catalog* cat, const spider_stations* sta, const spider_
 
   Prep& P = *out;
   P = Prep();
-  P.M = M; P.N = N; P.S = S; P.B = B; P.NB = (N + B - 1) / B;
+  P.M = M; P.N = N; P.S = S; P.B = B;
+  P.n_sub = n_sub;
+  P.sub_ev_off = evs;
+  P.sub_obs_off = obss;
 
-  // ---- event renumbering ----
-  if (cfg->reorder) {
-    P.ev_old = morton_order(cat->xyzt0, M);
-  } else {
-    P.ev_old.resize(M);
-    std::iota(P.ev_old.begin(), P.ev_old.end(), 0);
+  // ---- event renumbering (Morton order inside each sub-problem) ----
+  P.ev_old.resize(M);
+  P.ev_sub.resize(M);
+  P.ev_local.resize(M);
+  for (int s = 0; s < n_sub; ++s) {
+    const int64_t e0 = evs[s], ne = evs[s + 1] - evs[s];
+    std::vector<int32_t> o;
+    if (cfg->reorder) {
+      o = morton_order(cat->xyzt0 + 4 * e0, ne);
+    } else {
+      o.resize(ne);
+      std::iota(o.begin(), o.end(), 0);
+    }
+    for (int64_t m = 0; m < ne; ++m) {
+      P.ev_old[e0 + m] = (int32_t)(e0 + o[m]);
+      P.ev_sub[e0 + m] = s;
+      P.ev_local[e0 + m] = o[m];
+    }
   }
   std::vector<int32_t> rank(M);
   for (int64_t m = 0; m < M; ++m) rank[P.ev_old[m]] = (int32_t)m;
@@ -252,7 +283,20 @@ int prepare(const spider_catalog* cat, const spider_stations* sta, const spider_
     });
   }
 
-  // ---- blocks: local nodes, local indices, half-edge lists ----
+  // ---- blocks: cut per sub-problem, then local nodes, local indices, half-edge lists ----
+  P.sub_blk_off.assign(n_sub + 1, 0);
+  P.blk_e0.clear();
+  P.blk_sub.clear();
+  for (int s = 0; s < n_sub; ++s) {
+    P.sub_blk_off[s] = (int64_t)P.blk_sub.size();
+    for (int64_t e = obss[s]; e < obss[s + 1]; e += B) {
+      P.blk_e0.push_back((int32_t)e);
+      P.blk_sub.push_back(s);
+    }
+  }
+  P.sub_blk_off[n_sub] = (int64_t)P.blk_sub.size();
+  P.blk_e0.push_back((int32_t)N);
+  P.NB = (int64_t)P.blk_sub.size();
   const int64_t NB = P.NB;
   std::vector<std::vector<int32_t>> bnodes(NB);
   std::vector<std::vector<uint16_t>> bhe_beg(NB);
@@ -263,7 +307,7 @@ int prepare(const spider_catalog* cat, const spider_stations* sta, const spider_
     std::vector<int32_t> pi, pj;
     std::vector<uint16_t> deg, fill;
     for (int64_t blk = a; blk < b; ++blk) {
-      int64_t e0 = blk * B, ne = std::min(B, N - e0);
+      int64_t e0 = P.blk_e0[blk], ne = P.blk_e0[blk + 1] - e0;
       pi.resize(ne); pj.resize(ne);
       tmp.clear();
       for (int64_t e = 0; e < ne; ++e) {

@@ -12,7 +12,8 @@ namespace spider {
 //
 // Numbering: events are renumbered along a Morton curve of theta_0 (when
 // cfg->reorder), observations sorted by (i, j, k) in that numbering (stable),
-// then cut into blocks of B consecutive observations (the minibatch unit).
+// then cut into blocks of B consecutive observations (the minibatch unit; the
+// last block of each sub-problem may be shorter).
 //
 // A "pair" is an (event, station) combination met by some observation: the
 // node of the latent field b of Sec. 3.1 and the unit of travel-time work.
@@ -39,12 +40,28 @@ struct Prep {
   std::vector<int32_t> inc_off;      // P + 1: occurrences of a pair in blocks
   std::vector<int32_t> inc_q;        // Q: local node q of each occurrence (block-ascending)
   std::vector<int32_t> inc_b;        // Q: its block
+  // independent sub-problems (catalog x chain) sharing one device layout:
+  // disjoint event ranges, blocks never straddle two sub-problems
+  int32_t n_sub = 1;
+  std::vector<int32_t> blk_e0;       // NB + 1: first observation of each block
+  std::vector<int32_t> blk_sub;      // NB: sub-problem of each block
+  std::vector<int64_t> sub_ev_off;   // n_sub + 1 (events, new numbering = caller ranges)
+  std::vector<int64_t> sub_blk_off;  // n_sub + 1
+  std::vector<int64_t> sub_obs_off;  // n_sub + 1
+  std::vector<int32_t> ev_sub;       // M: sub-problem of each event
+  std::vector<int32_t> ev_local;     // M: caller index of the event inside its sub-problem
 };
 
 // Validates the inputs (returns SPIDER_E_INVAL with a message on failure) and
 // fills `out`.  threads: worker threads for the O(N) passes (0 = hardware).
+// With ev_splits / obs_splits (n_sub + 1 prefix offsets each) the catalog is
+// the concatenation of n_sub independent sub-problems: the observations of
+// sub-problem s lie in [obs_splits[s], obs_splits[s+1]) and reference only
+// events in [ev_splits[s], ev_splits[s+1]).
 int prepare(const spider_catalog* cat, const spider_stations* sta, const spider_config* cfg,
-            Prep* out, std::string* err, int threads = 0);
+            Prep* out, std::string* err, int threads = 0,
+            const std::vector<int64_t>* ev_splits = nullptr,
+            const std::vector<int64_t>* obs_splits = nullptr);
 
 // The Morton order of the library (events new -> old); see prepare().
 std::vector<int32_t> morton_order(const double* xyzt, int64_t M);

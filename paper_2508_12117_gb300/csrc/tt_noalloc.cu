@@ -138,7 +138,7 @@ extern "C" int spider_tt_pairs_noalloc(const spider_net* net, int64_t P, const f
     TTOut o{stage, reinterpret_cast<float4*>(J)};
     // launch_tt sizes the FP32 MLP grid as 2 x (its SM argument): kNaCtas CTAs,
     // one scratch slot each
-    e = launch_tt(nv, ps, o, kNaCtas / 2, slots, st);
+    e = launch_tt(nv, ps, o, kNaCtas / 2, slots, st, 2);
   }
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(T_hi, sizeof(float), stage, sizeof(float2), sizeof(float), (size_t)P,

@@ -60,13 +60,46 @@ struct TTOut {
   float4* J;    // (dT/dx, dT/dy, dT/dz, 0), may be null
 };
 
+// Per-step parameters, read by the kernels from device memory (the host
+// writes them before each step, so a captured step graph can be relaunched).
+struct StepParams {
+  uint64_t seed;
+  float eps;
+  float noise_scale;
+  int32_t tag;
+  int32_t mode;          // 0: gradient only, 1: SGLD update
+  int32_t full;          // 1: every block of every sub-problem
+  int32_t pad;
+  int64_t sample_slot;   // -1: no sample this step
+};
+
 // Step state and tables.
 struct StepView {
   int64_t M, N, S, NB, B, P, Q;
   int L_max;
+  const StepParams* prm;
+  // sub-problems (catalog x chain); a single catalog is one sub-problem
+  int n_sub;
+  const int32_t* blk_e0;          // NB + 1 first observation of each block
+  const int32_t* blk_sub;         // NB
+  const int32_t* ev_sub;          // M
+  const int32_t* sub_blk_off;     // n_sub + 1
+  const int32_t* sub_sel_full;    // n_sub + 1 prefix of blocks selected per step, full batch
+  const int32_t* sub_sel_mb;      // n_sub + 1 prefix of blocks selected per step, minibatch
+  const int32_t* sub_nobs;        // n_sub observations
+  const int32_t* sub_nev;         // n_sub events
+  const int32_t* sub_chain;       // n_sub Philox counter word 1
+  const int32_t* sub_catalog;     // n_sub Philox counter word 2
+  int32_t* sub_nsel;              // n_sub observations in this step's minibatch
+  float4* sub_cen;                // n_sub centroid of the current state offset
+  int n_chunks;
+  const int32_t* chunk_ev0;       // n_chunks + 1 event chunks for the centroid sums
+  const int32_t* sub_chunk_off;   // n_sub + 1
+  float4* cen_chunk;              // n_chunks
   const float4* th0_hi;
   const float4* th0_lo;
   float4* dth;
+  const int32_t* ev_caller;   // caller's index of each (internal) event: the noise counter
   const float4* sta_hi;
   const float4* sta_lo;
   const int32_t* pair_ev;
@@ -141,7 +174,6 @@ struct StepView {
   double* dblk;      // FP64 sum r^2 per selected block (NB)
   double* dred;      // FP64 diagnostics partials, 4 x kMaxGrid
   double* dout;      // FP64 results: [0] loglik (scaled), [1] logprior, [2] logcen, [3] logpost
-  float4* cen_part;  // 2 x kMaxGrid centroid partial sums
   float4* samples;
   int64_t sample_cap;
   // constants
@@ -150,10 +182,10 @@ struct StepView {
   int whiten;       // kappa > 0
   float4 inv_sig_e2;   // 1 / sigma_e^2
   float4 inv_sig_c2;   // 1 / sigma_c^2
-  int cen_grid;     // CTAs of the event kernel (fixed: centroid partials)
-  uint32_t chain, catalog;
+  int cen_grid;     // CTAs of the event kernel
 };
 
 constexpr int kMaxGrid = 4096;
+constexpr int kCenChunk = 4096;   // events per centroid partial sum
 
 }  // namespace spider

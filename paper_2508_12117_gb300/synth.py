@@ -110,6 +110,32 @@ def spec(wid: int) -> Spec:
     raise ValueError(f"unknown workload id {wid}")
 
 
+def batch_specs(n: int = 16, minibatch: int = 1 << 18) -> List[Spec]:
+    """The batched workload: n catalogs of uneven sizes (events log-uniform in
+    [1k, 200k], stations U{20..150}, neighbours U{10..25}, 10 observing
+    stations per event, faults at the 1M-event catalog's density, N(0, 5 ms)
+    noise), all read through one 6 -> 4 x 128 network; minibatches of
+    `minibatch` observations per catalog."""
+    rng = np.random.default_rng(SEED_BASE + 5)
+    out = []
+    for c in range(n):
+        M = int(round(math.exp(rng.uniform(math.log(1000.0), math.log(200000.0)))))
+        S = int(rng.integers(20, 151))
+        K = int(rng.integers(10, 26))
+        nf = max(1, int(round(M / 2000)))
+        region = max(10.0, 150.0 * math.sqrt(nf / 500.0))
+        h = Hyper(sigma=0.005, eps=_eps_for(0.03, 10, 20.0), batch_n=minibatch)
+        out.append(Spec(f"batch{c:02d}-{M}ev", 50 + c, M, S, K, 10, "faults", n_faults=nf,
+                        region_km=region, medium="gradient", noise="normal", noise_s=0.005,
+                        forward="mlp", hidden=128, hyper=h))
+    return out
+
+
+def batch_network() -> dict:
+    """The network shared by the batched workload."""
+    return mlp_weights(128, SEED_BASE + 105)
+
+
 def scaled_spec(wid: int, n_events: int, n_faults: Optional[int] = None,
                 region_km: Optional[float] = None, n_stations: Optional[int] = None,
                 batch_n: Optional[int] = None, hidden: Optional[int] = None) -> Spec:

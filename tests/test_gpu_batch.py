@@ -1,0 +1,80 @@
+"""Many catalogs x chains in one context (one launch per kernel, one CUDA graph
+per SGLD step) reproduce independent single-catalog samplers and the oracle."""
+import numpy as np
+import pytest
+
+from oracle import spider_oracle as O
+from paper_2508_12117_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = 0x9E3779B97F4A7C15
+
+
+@pytest.fixture(scope="module")
+def cats():
+    a = synth.make_catalog(1)
+    b = synth.make_catalog(synth.scaled_spec(2, 700, n_faults=1, region_km=6.0, n_stations=12))
+    b.spec.forward = "homogeneous"      # one network for the whole batch
+    return [a, b]
+
+
+def test_batch_full_batch_matches_single_contexts(cats):
+    chains = 2
+    net = binding.Net(binding.TT_HOMOGENEOUS, v0=6.0)
+    cfg = binding.make_config(sigma=0.01, kappa=0.03, thin=1, sample_cap=4)
+    bat = binding.Context.batch(cats, chains, net, cfg)
+    g_b, lp_b = bat.spider_grad_logpost(0)
+    singles, off, lp_sum = [], 0, 0.0
+    for ci, cat in enumerate(cats):
+        for h in range(chains):
+            ctx = binding.Context(cat.init_xyzt, cat.i, cat.j, cat.k, cat.dt, cat.stations, net,
+                                  binding.make_config(sigma=0.01, kappa=0.03, chain=h, catalog=ci,
+                                                      thin=1, sample_cap=4))
+            g, lp = ctx.spider_grad_logpost(0)
+            assert np.array_equal(g_b[off:off + cat.M], g)          # bit for bit
+            lp_sum += lp
+            singles.append((ctx, off, cat))
+            off += cat.M
+    assert abs(lp_b - lp_sum) <= 1e-9 * abs(lp_sum)
+    # SGLD in full batch: only the noise depends on the seed -> identical chains
+    for s in range(1, 6):
+        bat.spider_sgld_step(1e-4, s)
+        for ctx, _, _ in singles:
+            ctx.spider_sgld_step(1e-4, s)
+    th_b, step = bat.spider_get_state()
+    assert step == 5
+    for ctx, off, cat in singles:
+        th, _ = ctx.spider_get_state()
+        assert np.array_equal(th_b[off:off + cat.M], th)
+        ctx.close()
+    bat.close()
+
+
+def test_batch_minibatch_matches_oracle(cats):
+    chains = 2
+    net = binding.Net(binding.TT_HOMOGENEOUS, v0=6.0)
+    B, bn = 512, 1500
+    cfg = binding.make_config(sigma=0.01, kappa=0.03, batch_n=bn, block_obs=B)
+    bat = binding.Context.batch(cats, chains, net, cfg)
+    eps, seeds = 1e-5, [77, 78, 79]
+    for s in seeds:
+        bat.spider_sgld_step(eps, s)
+    th_b, _ = bat.spider_get_state()
+    off, sub = 0, 0
+    for ci, cat in enumerate(cats):
+        for h in range(chains):
+            P = O.problem_from_catalog(cat, batch_n=bn, model=O.Model("homogeneous", v0=6.0))
+            P.block_obs = B
+            P.sigma = 0.01
+            th = cat.init_xyzt.copy()
+            for s in seeds:
+                key = (s ^ ((GOLDEN * sub) & 0xFFFFFFFFFFFFFFFF)) & 0xFFFFFFFFFFFFFFFF
+                sel = np.sort(O.minibatch_obs(P.order, B, O.select_blocks(P.N, B, bn, key)))
+                _, g, _ = O.log_posterior(P, th, sel)
+                th = O.sgld_update(th, g, eps, O.langevin_noise(P.M, s, chain=h, catalog=ci))
+            dx = np.abs(th_b[off:off + cat.M, :3] - th[:, :3]).max() * 1e3
+            print(f"catalog {ci} chain {h}: max |dx| after {len(seeds)} minibatch steps {dx:.4f} m")
+            assert dx <= 0.05
+            off += cat.M
+            sub += 1
+    bat.close()

@@ -273,6 +273,24 @@ def test_sgld_chain_positions_after_1000_steps(cat1):
     ctx.close()
 
 
+def test_sgld_chain_with_shuffled_event_order(cat1):
+    """The noise counter follows the caller's event numbering (reading R6), so a
+    catalog listed in any order walks the same chain as the oracle."""
+    sh = synth.shuffled_events(cat1, seed=11)
+    eps = cat1.spec.hyper.eps
+    seeds = [500 + t for t in range(50)]
+    ctx = binding.Context.from_catalog(sh, chain=3, catalog=2)
+    for s in seeds:
+        ctx.spider_sgld_step(eps, s)
+    th, _ = ctx.spider_get_state()
+    P = O.problem_from_catalog(sh)
+    to, _ = O.run_chain(P, sh.init_xyzt, eps, seeds, chain=3, catalog=2)
+    dx_m = np.abs(th[:, :3] - to[:, :3]).max() * 1e3
+    print(f"shuffled order, 50 steps: max |dx| {dx_m:.4f} m")
+    assert dx_m <= 0.1
+    ctx.close()
+
+
 def test_exact_resume(cat1):
     eps = cat1.spec.hyper.eps
     a = binding.Context.from_catalog(cat1)
@@ -325,4 +343,31 @@ def test_two_event_catalog():
                   1e-5, np.array([0.5, 0.5, 0.5, 0.1]), np.array([0.01] * 4))
     L, go, _ = O.log_posterior(P, init)
     assert rel_l2(g, go) <= GRAD_TOL_FP32 and abs(lp - L) <= 1e-6 * abs(L)
+    ctx.close()
+
+
+def test_diagnostics_match_oracle(cat2):
+    """FP64 per-event gradient norms and the stochastic-gradient / injected-noise
+    variance ratio (Sec. 3.6) against the oracle's gradients."""
+    bn, eps, seed = 1 << 18, 2e-6, 5
+    ctx = binding.Context.from_catalog(cat2, batch_n=bn)
+    norms, ratio = ctx.spider_diagnostics(seed, eps)
+    P = O.problem_from_catalog(cat2, batch_n=bn)
+    _, g_mb, _ = O.log_posterior(P, cat2.init_xyzt, P.batch(seed))
+    _, g_full, _ = O.log_posterior(P, cat2.init_xyzt)
+    ref_norms = O.grad_norms(g_mb)
+    ref_ratio = eps * eps * np.mean((g_mb - g_full) ** 2) / (2 * eps)
+    assert rel_l2(norms, ref_norms) <= 1e-5
+    assert abs(ratio - ref_ratio) <= 1e-4 * ref_ratio
+    info = ctx.spider_info()
+    assert info["events"] == cat2.M and info["n_sub"] == 1 and info["components"] > 0
+    ctx.close()
+
+
+def test_step_runs_as_cuda_graph(cat1):
+    ctx = binding.Context.from_catalog(cat1)
+    ctx.spider_sgld_step(1e-4, 1)
+    ctx.spider_sgld_step(1e-4, 2)
+    info = ctx.spider_info()
+    assert info["graph"] == 1, info
     ctx.close()

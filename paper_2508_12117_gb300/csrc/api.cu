@@ -512,7 +512,8 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   AL(members, PP + 1);
   AL(lidx, PP);
   AL(big, PP);
-  AL(csr_lcol, 2 * N);
+  AL(chist, 512);
+  AL(corder, PP);
   AL(centries, PP);
   AL(ctier, PP);
   AL(Ap, PP);

@@ -428,6 +428,7 @@ constexpr int kCcRounds = 64;
 constexpr int kCompMax = 256;        // largest component solved by one warp
 constexpr int kCompEnt = 3072;       // largest CSR entry count cached by one warp
 constexpr int kCtaMax = 8192;        // largest component solved by one CTA
+constexpr int kCqBins = kCompMax + 1;   // work-list bins (see k_corder_scan)
 
 __device__ __forceinline__ int32_t cc_root(const int32_t* lab, int32_t u) {
   const volatile int32_t* vl = lab;
@@ -450,6 +451,7 @@ __global__ void __launch_bounds__(512) k_cc(StepView v) {
     v.ccount[u] = 0;
   }
   for (int i = gtid; i < kCcRounds; i += gstride) flags[i] = 0;
+  for (int i = gtid; i < kCqBins + 4; i += gstride) v.chist[i] = 0;
   if (!grid_barrier(v.counters)) return;
   int round = 0;
   for (; round < kCcRounds; ++round) {
@@ -524,7 +526,10 @@ __global__ void k_cc_place(StepView v) {
     const int32_t n = v.comp_off[c + 1] - v.comp_off[c];
     const int tier = (n <= kCompMax && v.centries[c] <= kCompEnt) ? 0 : (n <= kCtaMax ? 1 : 2);
     v.big[u] = tier == 2 ? 1 : 0;
-    if (u == v.comp_root[c]) v.ctier[c] = (uint8_t)tier;
+    if (u == v.comp_root[c]) {
+      v.ctier[c] = (uint8_t)tier;
+      if (tier < 2) atomicAdd(&v.chist[tier == 1 ? 0 : 1 + (kCompMax - n)], 1);
+    }
   }
 }
 
@@ -533,20 +538,6 @@ __device__ __forceinline__ float warp_allsum(float x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
-
-// One warp per component of at most kCompMax nodes and kCompEnt CSR entries:
-// the same iterative refinement as the grid-wide solver (double-float residual,
-// Jacobi-CG corrections to 1e-3) with the component's local CSR and vectors in
-// shared memory.  Members are sorted first so every sum runs in a fixed order.
-constexpr int kCompWarps = 4;
-
-struct WarpSmem {
-  int32_t mu[kCompMax];
-  float vec[8][kCompMax];          // zh, zl, diag, res, y, p, Ap, dz
-  int32_t lrp[kCompMax + 1];
-  uint8_t lcol[kCompEnt];
-  float lsw[kCompEnt];
-};
 
 __device__ void warp_sort(int32_t* a, int n2, int lane) {
   for (int k = 2; k <= n2; k <<= 1)
@@ -566,59 +557,388 @@ __device__ void warp_sort(int32_t* a, int n2, int lane) {
     }
 }
 
+// Two-value block reduction with one barrier: partials go to one of two
+// alternating buffers and every warp adds them up in the same order, so all
+// threads get the same (deterministic) sums.
+__device__ __forceinline__ float2 block_sum2(float a, float b, float2* sm /* 2 x 32 */, int& par) {
+  a = warp_allsum(a);
+  b = warp_allsum(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float2* buf = sm + 32 * par;
+  if (lane == 0) buf[wid] = make_float2(a, b);
+  __syncthreads();
+  float2 s = make_float2(0.f, 0.f);
+  for (int k = 0; k < nw; ++k) {
+    const float2 t = buf[k];
+    s.x += t.x;
+    s.y += t.y;
+  }
+  par ^= 1;
+  return s;
+}
+
+// Largest i with a[i] <= x for a sorted ascending, padded to n2 (a power of
+// two) with INT32_MAX, and a[0] <= x.
+__device__ __forceinline__ int bsearch_le(const int32_t* a, int n2, int32_t x) {
+  int i = 0;
+  for (int s = n2 >> 1; s > 0; s >>= 1)
+    if (a[i + s] <= x) i += s;
+  return i;
+}
+
+// Work list of the component solvers: the CTA tier first, then the warp tier by
+// decreasing size, so that the dynamic schedule starts the longest solves
+// first.  chist holds kCqBins counters (bin 0: CTA tier; bin 1 + kCompMax - n:
+// warp tier of size n), then [kCqBins] CTA cursor, [+1] warp cursor, [+2] start
+// of the warp tier, [+3] end of the list.
+__global__ void k_corder_scan(StepView v) {
+  __shared__ int sm[33];
+  int carry = 0;
+  for (int c = 0; c < kCqBins; c += blockDim.x) {
+    const int b = c + threadIdx.x;
+    const int val = b < kCqBins ? v.chist[b] : 0;
+    int total;
+    const int pre = block_exscan(val, sm, &total);
+    __syncthreads();
+    if (b < kCqBins) v.chist[b] = carry + pre;
+    carry += total;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    v.chist[kCqBins] = 0;
+    v.chist[kCqBins + 1] = 0;
+    v.chist[kCqBins + 2] = v.chist[1];
+    v.chist[kCqBins + 3] = carry;
+  }
+}
+
+__global__ void k_corder_fill(StepView v) {
+  const int32_t ncomp = v.counters[kCntComps];
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x) {
+    const int tier = v.ctier[c];
+    if (tier > 1) continue;
+    const int n = v.comp_off[c + 1] - v.comp_off[c];
+    const int bin = tier == 1 ? 0 : 1 + (kCompMax - n);
+    v.corder[atomicAdd(&v.chist[bin], 1)] = c;
+  }
+}
+
+// One warp per component of at most kCompMax nodes and kCompEnt CSR entries,
+// taken from the work list.  Members are sorted first so that every sum runs in
+// a fixed order; the component's CSR is cached in shared memory with local
+// column indices.  Up to kDenseMax nodes (and kDenseEnt entries) the matrix is
+// factorised (dense Cholesky, FP32) and z refined with the double-float
+// residual; otherwise (or when the factorisation fails) the same refinement
+// takes Jacobi-CG corrections to 1e-3.
+constexpr int kCompWarps = 4;
+constexpr int kDenseMax = 96;
+constexpr int kDenseEnt = 640;
+constexpr int kDenseSlots = kDenseMax / 32;
+
+struct WarpSmem {
+  int32_t mu[kCompMax];              // sorted members, padded to a power of two
+  int32_t lrp[kCompMax + 1];         // local row pointers, padded
+  union {
+    struct {
+      float vec[8][kCompMax];        // zh, zl, diag, res, y, p, Ap, dz (row starts while loading)
+      float lsw[kCompEnt];
+      uint8_t lcol[kCompEnt];
+    } it;
+    struct {
+      float L[kDenseMax * (kDenseMax + 1) / 2];   // packed lower triangle, column-major
+      float zh[kDenseMax], zl[kDenseMax], rdiag[kDenseMax];
+      int32_t rp0[kDenseMax];
+      float lsw[kDenseEnt];
+      uint8_t lcol[kDenseEnt];
+    } dn;
+  };
+};
+
+// Sorted members and the component's local CSR: row pointers by a warp scan of
+// the row lengths, then every entry (in parallel) its neighbour's local index.
+__device__ int warp_load_comp(const StepView& v, int32_t off, int n, int n2, int32_t* mu, int32_t* lrp,
+                              int32_t* rp0, uint8_t* lcol, float* lsw, int lane) {
+  for (int i = lane; i < n2; i += 32) mu[i] = i < n ? v.members[off + i] : 0x7FFFFFFF;
+  __syncwarp();
+  warp_sort(mu, n2, lane);
+  int carry = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    int len = 0;
+    if (i < n) {
+      const int32_t u = mu[i];
+      const int32_t r0 = v.rowptr[u];
+      len = v.rowptr[u + 1] - r0;
+      rp0[i] = r0;
+    }
+    int x = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < n) lrp[i] = carry + x - len;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  for (int i = n + 1 + lane; i < n2; i += 32) lrp[i] = 0x7FFFFFFF;
+  if (lane == 0) lrp[n] = carry;
+  __syncwarp();
+  const int E = carry;
+  for (int e0 = 0; e0 < E; e0 += 4 * 32) {
+    int32_t col[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + 32 * q + lane;
+      col[q] = 0;
+      if (e < E) {
+        const int row = bsearch_le(lrp, n2, e);
+        const int32_t t = rp0[row] + (e - lrp[row]);
+        col[q] = v.csr_col[t];
+        if (lsw) lsw[e] = v.csr_sw[t];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + 32 * q + lane;
+      if (e < E) lcol[e] = (uint8_t)bsearch_le(mu, n2, col[q]);
+    }
+  }
+  __syncwarp();
+  return E;
+}
+
+// Dense path: A = lambda I + B^T B assembled into the packed lower triangle
+// (column-major: column j holds rows j..n-1 from j n - j (j - 1) / 2, so that
+// lanes over rows read consecutive words), factorised A = L L^T left-looking:
+// column j is A(:, j) minus the dot products of the finished columns, each lane
+// one row (two interleaved partial sums), the pivot from a running sum of
+// squares per row.  z is then refined: residual in double-float, correction by
+// the two triangular solves (rows held in registers, the pivot broadcast by
+// shuffle).  NS is the number of 32-row slots (n <= 32 NS).  Returns the
+// refinement rounds, or -1 when a pivot is not positive or the refinement
+// stalls (z is then unusable).
+__device__ __forceinline__ int cm_off(int j, int n) { return j * n - (j * (j - 1)) / 2; }
+
+// rows i = j + 1 + lane + 32 s (s < NA) of column j: sum over p < j of L(i, p) L(j, p)
+template <int NA>
+__device__ __forceinline__ void dense_col_dots(const float* L, int n, int j, int lane, float* out) {
+  float a0[NA], a1[NA];
+  int ro[NA];
+#pragma unroll
+  for (int s = 0; s < NA; ++s) {
+    a0[s] = 0.f;
+    a1[s] = 0.f;
+    const int i = j + 1 + lane + 32 * s;
+    ro[s] = i < n ? i : j;            // rows past the end read row j (in bounds) and are dropped
+  }
+  int cb = 0;                         // column p starts at cb + p
+  int p = 0;
+  for (; p + 1 < j; p += 2) {
+    const int cb1 = cb + n - p - 1;
+    const float l0 = L[cb + j], l1 = L[cb1 + j];
+#pragma unroll
+    for (int s = 0; s < NA; ++s) {
+      a0[s] = fmaf(L[cb + ro[s]], l0, a0[s]);
+      a1[s] = fmaf(L[cb1 + ro[s]], l1, a1[s]);
+    }
+    cb = cb1 + n - p - 2;
+  }
+  if (p < j) {
+    const float l0 = L[cb + j];
+#pragma unroll
+    for (int s = 0; s < NA; ++s) a0[s] = fmaf(L[cb + ro[s]], l0, a0[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < NA; ++s) out[s] = a0[s] + a1[s];
+}
+
+template <int NS>
+__device__ int warp_dense_solve(const StepView& v, WarpSmem& S, int n, float tol, int lane) {
+  auto& D = S.dn;
+  float* L = D.L;
+  float* sq = D.zh;                   // sum of squares of each row's finished entries
+  const float lam = v.lam;
+  const int tot = n * (n + 1) / 2;
+  for (int t = lane; t < tot; t += 32) L[t] = 0.f;
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    L[cm_off(i, n)] = v.diag[S.mu[i]];
+    sq[i] = 0.f;
+    for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
+      const int lc = D.lcol[l];
+      if (lc < i) {
+        const float sw = D.lsw[l];
+        float* a = L + cm_off(lc, n) + (i - lc);
+        *a = fmaf(-sw, sw, *a);
+      }
+    }
+  }
+  __syncwarp();
+  for (int j = 0; j < n; ++j) {
+    const int cj = cm_off(j, n);
+    const float d = L[cj] - sq[j];
+    if (!(d > 0.f)) return -1;
+    const float ljj = sqrtf(d);
+    const float inv = 1.0f / ljj;
+    const int na = (n - j + 30) >> 5;   // slots holding rows j+1..n-1
+    float dots[NS];
+    if (NS >= 3 && na >= 3) dense_col_dots<NS >= 3 ? 3 : 1>(L, n, j, lane, dots);
+    else if (NS >= 2 && na == 2) dense_col_dots<NS >= 2 ? 2 : 1>(L, n, j, lane, dots);
+    else if (na == 1) dense_col_dots<1>(L, n, j, lane, dots);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int i = j + 1 + lane + 32 * s;
+      if (s < na && i < n) {
+        const float lij = (L[cj + i - j] - dots[s]) * inv;
+        L[cj + i - j] = lij;
+        sq[i] = fmaf(lij, lij, sq[i]);
+      }
+    }
+    if (lane == 0) {
+      L[cj] = ljj;
+      D.rdiag[j] = inv;
+    }
+    __syncwarp();
+  }
+  float bb = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float b = v.rhs[S.mu[i]];
+    bb = fmaf(b, b, bb);
+    D.zh[i] = 0.f;
+    D.zl[i] = 0.f;
+  }
+  bb = warp_allsum(bb);
+  __syncwarp();
+  if (!(bb > 0.f)) return 0;
+  int rowb[NS];                       // L(q, i) = L[rowb + q] for i < q
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int i = lane + 32 * s;
+    rowb[s] = cm_off(i, n) - i;
+  }
+  float prev = 0.f;
+  for (int round = 0; round < 10; ++round) {
+    float rr = 0.f;
+    float yr[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int i = lane + 32 * s;
+      yr[s] = 0.f;
+      if (i >= n) continue;
+      const int32_t u = S.mu[i];
+      float r;
+      if (round == 0) {
+        r = v.rhs[u] + v.rhs_lo[u];
+      } else {
+        const df32 zu = {D.zh[i], D.zl[i]};
+        df32 acc = {0.f, 0.f};
+        for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
+          const int lc = D.lcol[l];
+          const float sw = D.lsw[l];
+          acc = df_add(acc, df_mul(df_two_prod(sw, sw), df_add(zu, df32{-D.zh[lc], -D.zl[lc]})));
+        }
+        df32 rd = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zu, -lam));
+        rd = df_add(rd, df32{-acc.hi, -acc.lo});
+        r = rd.hi;
+      }
+      yr[s] = r;
+      rr = fmaf(r, r, rr);
+    }
+    rr = warp_allsum(rr);
+    if (rr <= tol * tol * bb) return round;
+    if (round > 0 && !(rr < 0.25f * prev)) return -1;
+    prev = rr;
+    // L w = r (column sweep: column p is contiguous)
+    int cp = 0;
+    for (int p = 0; p < n; ++p) {
+      const int sp = p >> 5;
+      float mine = yr[0];
+#pragma unroll
+      for (int s = 1; s < NS; ++s) mine = sp == s ? yr[s] : mine;
+      const float wp = __shfl_sync(0xffffffffu, mine, p & 31) * D.rdiag[p];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const int i = lane + 32 * s;
+        if (i == p) yr[s] = wp;
+        else if (i > p && i < n) yr[s] = fmaf(-L[cp + i - p], wp, yr[s]);
+      }
+      cp += n - p;
+    }
+    // L^T d = w
+    for (int q = n - 1; q >= 0; --q) {
+      const int sq_ = q >> 5;
+      float mine = yr[0];
+#pragma unroll
+      for (int s = 1; s < NS; ++s) mine = sq_ == s ? yr[s] : mine;
+      const float dq = __shfl_sync(0xffffffffu, mine, q & 31) * D.rdiag[q];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const int i = lane + 32 * s;
+        if (i == q) yr[s] = dq;
+        else if (i < q) yr[s] = fmaf(-L[rowb[s] + q], dq, yr[s]);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int i = lane + 32 * s;
+      if (i < n) {
+        const df32 zn = df_add_f(df32{D.zh[i], D.zl[i]}, yr[s]);
+        D.zh[i] = zn.hi;
+        D.zl[i] = zn.lo;
+      }
+    }
+    __syncwarp();
+  }
+  return -1;
+}
+
 __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int max_it, float tol) {
   extern __shared__ __align__(16) uint8_t smem_w[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_w)[w];
-  const int32_t ncomp = v.counters[kCntComps];
   const float lam = v.lam;
   int32_t* mu = S.mu;
-  float* zh = S.vec[0];
-  float* zl = S.vec[1];
-  float* dg = S.vec[2];
-  float* rs = S.vec[3];
-  float* yv = S.vec[4];
-  float* pv = S.vec[5];
-  float* ap = S.vec[6];
-  float* dz = S.vec[7];
+  float* zh = S.it.vec[0];
+  float* zl = S.it.vec[1];
+  float* dg = S.it.vec[2];
+  float* rs = S.it.vec[3];
+  float* yv = S.it.vec[4];
+  float* pv = S.it.vec[5];
+  float* ap = S.it.vec[6];
+  float* dz = S.it.vec[7];
+  const int32_t w_beg = v.chist[kCqBins + 2], w_end = v.chist[kCqBins + 3];
   int max_iters = 0;
-  for (int32_t c = blockIdx.x * kCompWarps + w; c < ncomp; c += gridDim.x * kCompWarps) {
-    if (v.ctier[c] != 0) continue;
+  for (;;) {
+    int32_t k = 0;
+    if (lane == 0) k = atomicAdd(&v.chist[kCqBins + 1], 1);
+    k = __shfl_sync(0xffffffffu, k, 0) + w_beg;
+    if (k >= w_end) break;
+    const int32_t c = v.corder[k];
     const int32_t off = v.comp_off[c];
     const int n = v.comp_off[c + 1] - off;
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
-    for (int i = lane; i < n2; i += 32) mu[i] = i < n ? v.members[off + i] : 0x7FFFFFFF;
-    __syncwarp();
-    warp_sort(mu, n2, lane);
-    for (int i = lane; i < n; i += 32) v.lidx[mu[i]] = i;
-    // local row pointers (warp scan over the sorted members)
-    int carry = 0;
-    for (int base = 0; base < n; base += 32) {
-      const int i = base + lane;
-      const int len = i < n ? v.rowlen[mu[i]] : 0;
-      int x = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+    if (n <= kDenseMax && v.centries[c] <= kDenseEnt) {
+      warp_load_comp(v, off, n, n2, mu, S.lrp, S.dn.rp0, S.dn.lcol, S.dn.lsw, lane);
+      const int rounds = n <= 32   ? warp_dense_solve<1>(v, S, n, tol, lane)
+                         : n <= 64 ? warp_dense_solve<2>(v, S, n, tol, lane)
+                                   : warp_dense_solve<kDenseSlots>(v, S, n, tol, lane);
+      __syncwarp();
+      if (rounds >= 0) {
+        for (int i = lane; i < n; i += 32) {
+          v.z[mu[i]] = S.dn.zh[i];
+          v.z_lo[mu[i]] = S.dn.zl[i];
+        }
+        __syncwarp();
+        continue;
       }
-      if (i < n) S.lrp[i] = carry + x - len;
-      carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    if (lane == 0) S.lrp[n] = carry;
-    __syncwarp();
+    // iterative path (row starts in dz while loading)
+    warp_load_comp(v, off, n, n2, mu, S.lrp, reinterpret_cast<int32_t*>(dz), S.it.lcol, S.it.lsw, lane);
     for (int i = lane; i < n; i += 32) {
-      const int32_t u = mu[i];
-      const int32_t t0 = v.rowptr[u];
-      const int l0 = S.lrp[i], l1 = S.lrp[i + 1];
-      for (int l = l0; l < l1; ++l) {
-        S.lcol[l] = (uint8_t)v.lidx[v.csr_col[t0 + (l - l0)]];
-        S.lsw[l] = v.csr_sw[t0 + (l - l0)];
-      }
       zh[i] = 0.f;
       zl[i] = 0.f;
-      dg[i] = v.diag[u];
+      dg[i] = v.diag[mu[i]];
     }
     __syncwarp();
     float bb = 0.f;
@@ -640,8 +960,8 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
           const df32 zu = {zh[i], zl[i]};
           df32 acc = {0.f, 0.f};
           for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
-            const int lc = S.lcol[l];
-            const float sw = S.lsw[l];
+            const int lc = S.it.lcol[l];
+            const float sw = S.it.lsw[l];
             acc = df_add(acc, df_mul(df_two_prod(sw, sw), df_add(zu, df32{-zh[lc], -zl[lc]})));
           }
           df32 rd = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zu, -lam));
@@ -668,8 +988,8 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
           const float yu = yv[i];
           float sacc = 0.f;
           for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
-            const float sw = S.lsw[l];
-            sacc = fmaf(sw * sw, yu - yv[S.lcol[l]], sacc);
+            const float sw = S.it.lsw[l];
+            sacc = fmaf(sw * sw, yu - yv[S.it.lcol[l]], sacc);
           }
           const float ay = fmaf(lam, yu, sacc);
           const float pn = first ? yu : fmaf(beta, pv[i], yu);
@@ -715,42 +1035,214 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
     if (it > max_iters) max_iters = it;
   }
   if (lane == 0 && max_iters > 0) atomicMax(&v.counters[kCntCompIters], max_iters);
+  // the CTA tier (launched before this kernel) is complete and visible once this returns
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// One CTA per component of at most kCtaMax nodes (vectors in global memory,
-// indexed by unique pair; block-level reductions over the sorted members).
+// One CTA per component of more than kCompMax (or kCompEnt entries) and at most
+// kCtaMax nodes, taken from the work list.  Up to kCtaSm nodes and kCtaSmEnt
+// entries the component's CSR and vectors live in shared memory (local column
+// indices, two-value reductions with one barrier); larger components keep
+// their vectors in global memory, indexed by unique pair.
 constexpr int kCtaThreads = 512;
+constexpr int kCtaSm = 1024;
+constexpr int kCtaSmEnt = 11264;
+
+struct CtaSmem {
+  int32_t mu[kCtaSm];
+  int32_t lrp[kCtaSm + 4];
+  float vec[8][kCtaSm];             // zh, zl, diag, res, y, p, Ap, dz (row starts while loading)
+  float lsw[kCtaSmEnt];
+  uint16_t lcol[kCtaSmEnt];
+};
+static_assert(sizeof(CtaSmem) >= kCtaMax * sizeof(int32_t), "member sort buffer");
+
+__device__ void cta_sort(int32_t* mu, int n2) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int32_t x = mu[i], y = mu[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            mu[i] = y;
+            mu[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// shared-memory CTA solve; returns the inner iterations
+__device__ int cta_solve_smem(const StepView& v, CtaSmem& S, int32_t off, int n, int n2, int max_it, float tol,
+                              float2* red2, int* smi) {
+  const float lam = v.lam;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int32_t* mu = S.mu;
+  float* zh = S.vec[0];
+  float* zl = S.vec[1];
+  float* dg = S.vec[2];
+  float* rs = S.vec[3];
+  float* yv = S.vec[4];
+  float* pv = S.vec[5];
+  float* ap = S.vec[6];
+  float* dz = S.vec[7];
+  int32_t* rp0 = reinterpret_cast<int32_t*>(dz);
+  for (int i = tid; i < n2; i += nt) mu[i] = i < n ? v.members[off + i] : 0x7FFFFFFF;
+  __syncthreads();
+  cta_sort(mu, n2);
+  int carry = 0;
+  for (int base = 0; base < n; base += nt) {
+    const int i = base + tid;
+    int len = 0;
+    if (i < n) {
+      const int32_t u = mu[i];
+      const int32_t r0 = v.rowptr[u];
+      len = v.rowptr[u + 1] - r0;
+      rp0[i] = r0;
+    }
+    int total;
+    const int pre = block_exscan(len, smi, &total);
+    if (i < n) S.lrp[i] = carry + pre;
+    carry += total;
+  }
+  for (int i = n + 1 + tid; i < n2; i += nt) S.lrp[i] = 0x7FFFFFFF;
+  if (tid == 0) S.lrp[n] = carry;
+  __syncthreads();
+  const int E = carry;
+  for (int e = tid; e < E; e += nt) {
+    const int row = bsearch_le(S.lrp, n2, e);
+    const int32_t t = rp0[row] + (e - S.lrp[row]);
+    S.lsw[e] = v.csr_sw[t];
+    S.lcol[e] = (uint16_t)bsearch_le(mu, n2, v.csr_col[t]);
+  }
+  __syncthreads();
+  int par = 0;
+  float bb = 0.f;
+  for (int i = tid; i < n; i += nt) {
+    const float b = v.rhs[mu[i]];
+    bb = fmaf(b, b, bb);
+    zh[i] = 0.f;
+    zl[i] = 0.f;
+    dg[i] = v.diag[mu[i]];
+  }
+  bb = block_sum2(bb, 0.f, red2, par).x;
+  const float outer_thr = tol * tol * bb;
+  int it = 0;
+  for (int round = 0; round < 8 && bb > 0.f && it < max_it; ++round) {
+    float rz = 0.f, rr0 = 0.f;
+    for (int i = tid; i < n; i += nt) {
+      const int32_t u = mu[i];
+      float r;
+      if (round == 0) {
+        r = v.rhs[u] + v.rhs_lo[u];
+      } else {
+        const df32 zu = {zh[i], zl[i]};
+        df32 acc = {0.f, 0.f};
+        for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
+          const int lc = S.lcol[l];
+          const float sw = S.lsw[l];
+          acc = df_add(acc, df_mul(df_two_prod(sw, sw), df_add(zu, df32{-zh[lc], -zl[lc]})));
+        }
+        df32 rd = df_add(df32{v.rhs[u], v.rhs_lo[u]}, df_mul_f(zu, -lam));
+        rd = df_add(rd, df32{-acc.hi, -acc.lo});
+        r = rd.hi;
+      }
+      const float y = r / dg[i];
+      rs[i] = r;
+      yv[i] = y;
+      dz[i] = 0.f;
+      rz = fmaf(r, y, rz);
+      rr0 = fmaf(r, r, rr0);
+    }
+    const float2 s0 = block_sum2(rz, rr0, red2, par);
+    rz = s0.x;
+    if (s0.y <= outer_thr) break;
+    const float inner_thr = 1e-6f * s0.y;
+    float beta = 0.f;
+    bool first = true;
+    while (it < max_it) {
+      float dot = 0.f;
+      for (int i = tid; i < n; i += nt) {
+        const float yu = yv[i];
+        float sacc = 0.f;
+        for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
+          const float sw = S.lsw[l];
+          sacc = fmaf(sw * sw, yu - yv[S.lcol[l]], sacc);
+        }
+        const float ay = fmaf(lam, yu, sacc);
+        const float pn = first ? yu : fmaf(beta, pv[i], yu);
+        const float apn = first ? ay : fmaf(beta, ap[i], ay);
+        pv[i] = pn;
+        ap[i] = apn;
+        dot = fmaf(pn, apn, dot);
+      }
+      const float pap = block_sum2(dot, 0.f, red2, par).x;
+      const float alpha = pap > 0.f ? rz / pap : 0.f;
+      float rzn = 0.f, rr = 0.f;
+      for (int i = tid; i < n; i += nt) {
+        dz[i] = fmaf(alpha, pv[i], dz[i]);
+        const float r = fmaf(-alpha, ap[i], rs[i]);
+        rs[i] = r;
+        const float y = r / dg[i];
+        yv[i] = y;
+        rzn = fmaf(r, y, rzn);
+        rr = fmaf(r, r, rr);
+      }
+      const float2 s1 = block_sum2(rzn, rr, red2, par);
+      ++it;
+      if (s1.y <= inner_thr || !(pap > 0.f)) break;
+      beta = s1.x / rz;
+      rz = s1.x;
+      first = false;
+    }
+    for (int i = tid; i < n; i += nt) {
+      const df32 zn = df_add_f(df32{zh[i], zl[i]}, dz[i]);
+      zh[i] = zn.hi;
+      zl[i] = zn.lo;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) {
+    v.z[mu[i]] = zh[i];
+    v.z_lo[mu[i]] = zl[i];
+  }
+  return it;
+}
 
 __global__ void __launch_bounds__(kCtaThreads) k_comp_solve_cta(StepView v, int max_it, float tol) {
-  __shared__ int32_t mu[kCtaMax];
+  extern __shared__ __align__(16) uint8_t smem_c[];
+  CtaSmem& S = *reinterpret_cast<CtaSmem*>(smem_c);
   __shared__ float smr[33];
-  const int32_t ncomp = v.counters[kCntComps];
+  __shared__ float2 red2[64];
+  __shared__ int smi[33];
+  __shared__ int32_t s_k;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const float lam = v.lam;
+  const int32_t c_end = v.chist[kCqBins + 2];
   int max_iters = 0;
-  for (int32_t c = blockIdx.x; c < ncomp; c += gridDim.x) {
-    if (v.ctier[c] != 1) continue;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_k = atomicAdd(&v.chist[kCqBins], 1);
+    __syncthreads();
+    const int32_t k = s_k;
+    if (k >= c_end) break;
+    const int32_t c = v.corder[k];
     const int32_t off = v.comp_off[c];
     const int n = v.comp_off[c + 1] - off;
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
-    __syncthreads();
+    if (n <= kCtaSm && v.centries[c] <= kCtaSmEnt) {
+      const int it = cta_solve_smem(v, S, off, n, n2, max_it, tol, red2, smi);
+      if (it > max_iters) max_iters = it;
+      continue;
+    }
+    int32_t* mu = reinterpret_cast<int32_t*>(smem_c);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) mu[i] = i < n ? v.members[off + i] : 0x7FFFFFFF;
     __syncthreads();
-    for (int k = 2; k <= n2; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-          const int l = i ^ j;
-          if (l > i) {
-            const int32_t x = mu[i], y = mu[l];
-            const bool up = (i & k) == 0;
-            if ((x > y) == up) {
-              mu[i] = y;
-              mu[l] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
+    cta_sort(mu, n2);
     float bb = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int32_t u = mu[i];
@@ -1225,6 +1717,9 @@ cudaError_t configure_step_kernels(const StepView& v) {
   if ((e = cudaFuncSetAttribute(k_comp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(kCompWarps * sizeof(WarpSmem)))))
     return e;
+  if ((e = cudaFuncSetAttribute(k_comp_solve_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(CtaSmem))))
+    return e;
   return cudaSuccess;
 }
 
@@ -1276,8 +1771,25 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
   k_scan_c<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part, v.comp_off);
   k_cc_fill<<<parts, kThreads, 0, st>>>(v);
   k_cc_place<<<parts, kThreads, 0, st>>>(v);
-  k_comp_solve<<<warp_mult * parts, kCompWarps * 32, kCompWarps * sizeof(WarpSmem), st>>>(v, max_it, tol);
-  k_comp_solve_cta<<<cta_mult * parts, kCtaThreads, 0, st>>>(v, max_it, tol);
+  k_corder_scan<<<1, 512, 0, st>>>(v);
+  k_corder_fill<<<parts, kThreads, 0, st>>>(v);
+  // the CTA tier first; the warp tier may start as soon as every CTA of it has
+  // begun (programmatic dependent launch) and waits for it before it exits
+  k_comp_solve_cta<<<cta_mult * parts, kCtaThreads, sizeof(CtaSmem), st>>>(v, max_it, tol);
+  {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(warp_mult * parts));
+    lc.blockDim = dim3(kCompWarps * 32);
+    lc.dynamicSmemBytes = kCompWarps * sizeof(WarpSmem);
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelEx(&lc, k_comp_solve, v, max_it, tol);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   StepView vv = v;

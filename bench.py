@@ -190,7 +190,9 @@ def run_ours(args, rank, world):
         peak = pk["bf16_tflops_sustained"] * (2.0 if args.precision == "fp8" else 1.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "k_tt_mlp_tc", "peak_source": f"bf16 sustained, {which}"}
+                "kernel": "k_tt_mlp_tc",
+                "peak_source": (f"bf16 sustained x 2 (nominal fp8/bf16 dense ratio), {which}"
+                                if args.precision == "fp8" else f"bf16 sustained, {which}")}
     steps_s = world * K / (ms_dev * 1e-3)
     state_bytes = cat.M * 16
     line = {

@@ -2,7 +2,7 @@
 // source Jacobian for tiles of 128 (event, station) pairs (Sec. 2.1, Sec. 3.2).
 //
 //   layer 1 (6 -> H, FP32, CUDA cores)  h1 = silu(W1 [x; s] + b1)
-//   layers 2..4 (H x H, BF16 x BF16 -> FP32 in TMEM)  h_l = silu(W_l h_{l-1} + b_l)
+//   layers 2..4 (H x H, BF16 x BF16 or E4M3 x E4M3 -> FP32 in TMEM)  h_l = silu(W_l h_{l-1} + b_l)
 //   output (H -> 1, FP32)  tau = w5 . h4 + b5,  T = |x - s| tau  (double-float outer product)
 //   reverse sweep (H x H, BF16 -> FP32 in TMEM)
 //       delta4 = w5 * silu'(z4);  delta_{l-1} = (W_l^T delta_l) * silu'(z_{l-1})
@@ -18,17 +18,26 @@
 //              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
 // TMEM (2H columns): [0, H) accumulator, [H, 3H/2) silu'(z1) and [3H/2, 2H)
 // silu'(z2) packed as BF16 pairs; silu'(z3) sits in shared memory.
+// FP8 form (kind::f8f6f4, E4M3 operands, FP32 accumulation): the weight images
+// carry one scale per output column (max |W| / 448); each activation row is
+// quantised with its own scale, from a first pass over the accumulator that
+// bounds the row's largest magnitude (the two threads holding a row exchange
+// their halves' bounds through a 64-arrival mbarrier); delta4 = w5 * silu'(z4)
+// uses the fixed bound 1.1 max |w5|.  The accumulator of the next layer is
+// rescaled by (row scale) x (column scale) before bias and activation.
 // Every wait is bounded (2 s on the global timer): on timeout the kernel sets
 // SPIDER_E_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "dfloat.cuh"
 #include "kernels.h"
 #include "pairs.cuh"
+#include "quant.h"
 #include "spider.h"
 
 namespace spider {
@@ -41,12 +50,13 @@ constexpr int kTcThreads = kEpiThreads + 64;
 constexpr int kStages = 2;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
-template <int H>
+template <int H, bool F8>
 struct Cfg {
-  static constexpr int KB = H / 64;                 // K-blocks of 64 BF16 per layer
+  static constexpr int EB = F8 ? 1 : 2;             // bytes per operand element
+  static constexpr int KB = H * EB / 128;           // K-blocks (128-byte rows) per layer
   static constexpr int kChunk = H * 128;            // bytes of one weight K-block (H rows x 128 B)
-  static constexpr int kImage = H * H * 2;          // bytes of one weight image
-  static constexpr int kA = kRows * H * 2;          // activations, SW128 K-major
+  static constexpr int kImage = H * H * EB;         // bytes of one weight image
+  static constexpr int kA = kRows * H * EB;         // activations, SW128 K-major
   static constexpr int kD3 = kRows * H * 2;         // silu'(z3), BF16
   static constexpr int kHalf = H / 2;               // columns per epilogue thread
   static constexpr int kTmemCols = 2 * H;
@@ -56,9 +66,11 @@ struct Cfg {
   static constexpr int oB = oA + kA;
   static constexpr int oD3 = oB + kStages * kChunk;
   static constexpr int oPar = oD3 + kD3;                  // W1 (6H), b1, b2, b3, b4, w5 (5H) floats
-  static constexpr int oRed = oPar + 11 * H * 4;          // [4][2][kRows] floats
+  static constexpr int oSc = oPar + 11 * H * 4;           // FP8: column scales of the 6 images (6H floats)
+  static constexpr int oXch = oSc + (F8 ? 6 * H * 4 : 0); // FP8: row-bound exchange [2][2][kRows] floats
+  static constexpr int oRed = oXch + (F8 ? 4 * kRows * 4 : 0);   // [4][2][kRows] floats
   static constexpr int oBar = oRed + 4 * 2 * kRows * 4;   // mbarriers
-  static constexpr int oMisc = oBar + 8 * 8;              // tmem base, abort flag
+  static constexpr int oMisc = oBar + 16 * 8;             // tmem base, abort flag
   static constexpr int kSmem = oMisc + 16 + 1024;         // + alignment slack
 };
 
@@ -128,13 +140,28 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: E4M3 A and B (both K-major), FP32 D, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+template <bool F8>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+  if constexpr (F8) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
@@ -196,13 +223,39 @@ __device__ __forceinline__ uint32_t a_off(int r, int k) {
   const int kb = k >> 6, j = (k >> 3) & 7;
   return (uint32_t)(kb * (kRows * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + (k & 7) * 2);
 }
+// the same for 8-bit elements (K-blocks of 128)
+__device__ __forceinline__ uint32_t a_off8(int r, int k) {
+  const int kb = k >> 7, j = (k >> 4) & 7;
+  return (uint32_t)(kb * (kRows * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + (k & 15));
+}
+
+// four FP32 values -> four E4M3 bytes (round to nearest even, saturating), first value in the low byte
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// FP8: largest magnitude bound of a row over both column halves (bounded wait)
+__device__ __forceinline__ bool pair_max(float& m, float* xch, uint64_t* xbar, uint32_t& xph, int half, int r,
+                                         volatile int* abort_flag, int32_t* gerr) {
+  const int slot = (int)(xph & 1);
+  xch[(slot * 2 + half) * kRows + r] = m;
+  mbar_arrive(xbar);
+  const bool got = mbar_wait(xbar, xph & 1, abort_flag, gerr);
+  xph ^= 1;
+  if (got) m = fmaxf(m, xch[(slot * 2 + (half ^ 1)) * kRows + r]);
+  return got;
+}
+
 // silu'(z3): 16-byte chunk c/8 of row r at ((c/8) * 128 + r) * 16
 __device__ __forceinline__ uint32_t d3_off(int r, int c) { return (uint32_t)(((c >> 3) * kRows + r) * 16); }
 
-template <int H>
+template <int H, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tt_mlp_tc(NetView net, PairSource src, TTOut out, const uint8_t* __restrict__ wimg, int32_t* gerr) {
-  using C = Cfg<H>;
+  using C = Cfg<H, F8>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm + C::oA;
@@ -213,6 +266,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float* pb = pb1 + H;       // b2, b3, b4
   float* pw5 = pb + 3 * H;
   float* red = reinterpret_cast<float*>(sm + C::oRed);
+  float* wsc = reinterpret_cast<float*>(sm + C::oSc);     // FP8 column scales [6][H]
+  float* xch = reinterpret_cast<float*>(sm + C::oXch);    // FP8 row-bound exchange
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::oBar);
   uint64_t* full = bars;           // [2] weight stage loaded
   uint64_t* empty = bars + 2;      // [2] weight stage consumed
@@ -220,6 +275,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* a_ready = bars + 5;    // epilogue done with TMEM reads + A written
   uint64_t* drain = bars + 6;      // MMA drain on abort
   uint64_t* red_ready = bars + 7;  // both column halves of every row reduced
+  uint64_t* xbar = bars + 8;       // [4] FP8 row-bound exchange of warps g and g + 4
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + C::oMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + C::oMisc + 4);
 
@@ -233,6 +289,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(a_ready, kEpiThreads);
     mbar_init(drain, 1);
     mbar_init(red_ready, kEpiThreads);
+    for (int q = 0; q < 4; ++q) mbar_init(&xbar[q], 64);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -244,6 +301,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     pb[2 * H + i] = net.bh[2][i];
     pw5[i] = net.W5[i];
   }
+  if constexpr (F8)
+    for (int i = threadIdx.x; i < 6 * H; i += blockDim.x) wsc[i] = net.tc_scale[i];
+  const float s4 = F8 ? net.tc_scale[6 * H] : 1.f;     // FP8 scale of delta4 = w5 * silu'(z4)
   if (warp == kEpiWarps + 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                  "r"((uint32_t)C::kTmemCols));
@@ -282,7 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == kEpiWarps + 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(H);
+      constexpr uint32_t idesc = F8 ? idesc_e4m3(H) : idesc_bf16(H);
       const uint32_t a_base = su32(sA), b_base = su32(sB);
       int64_t n = 0;        // weight chunks consumed
       uint32_t a_phase = 0;
@@ -301,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int k = 0; k < 4; ++k) {
               const uint64_t ad = sw128_desc(a_base + kb * (kRows * 128) + k * 32);
               const uint64_t bd = sw128_desc(b_base + s * C::kChunk + k * 32);
-              umma(tmem, ad, bd, idesc, (kb | k) ? 1u : 0u);
+              umma<F8>(tmem, ad, bd, idesc, (kb | k) ? 1u : 0u);
               ++issued;
             }
             umma_commit(&empty[s]);
@@ -323,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int r = g * 32 + lane;                       // tile row = TMEM lane
     const uint32_t lane_addr = tmem + ((uint32_t)(g * 32) << 16);
     const int c0 = half * C::kHalf;                    // first column of this thread
-    uint32_t acc_phase = 0, red_phase = 0;
+    uint32_t acc_phase = 0, red_phase = 0, xph = 0;
     for (int64_t t = 0; t < my_tiles; ++t) {
       const int64_t u0 = (blockIdx.x + t * gridDim.x) * kRows;
       const int64_t u = u0 + r;
@@ -338,111 +398,261 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           x[3 + c] = pg.rhi[c] + pg.rlo[c];
         }
       }
-      // layer 1 in FP32: h1 -> A (BF16), silu'(z1) -> TMEM [H, 3H/2)
-      for (int cc = 0; cc < C::kHalf; cc += 32) {
-        const int col = c0 + cc;
-        uint32_t hp[16], dp[16];
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          float z0 = pb1[col + i], z1 = pb1[col + i + 1];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            z0 = fmaf(pW1[(col + i) * 6 + c], x[c], z0);
-            z1 = fmaf(pW1[(col + i + 1) * 6 + c], x[c], z1);
-          }
-          float h0, d0, h1, d1;
-          silu_tc(z0, h0, d0);
-          silu_tc(z1, h1, d1);
-          hp[i / 2] = pack_bf16(h0, h1);
-          dp[i / 2] = pack_bf16(d0, d1);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
-              make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-        tmem_st16(lane_addr + H + col / 2, dp);
-      }
-      tmem_wait_st();
-      fence_async_smem();
-      tc_before();
-      mbar_arrive(a_ready);
-
       float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
       bool ok = true;
-      for (int layer = 0; layer < 6; ++layer) {
-        const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
-        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
-        acc_phase ^= 1;
-        tc_after();
-        for (int cc = 0; cc < C::kHalf; cc += 32) {
-          const int col = c0 + cc;
-          float v[32];
-          tmem_ld32(lane_addr + col, v);
-          tmem_wait_ld();
-          uint32_t hp[16], dp[16];
-          if (layer < 3) {
-            // forward layers 2..4
-            const float* bias = pb + layer * H;
+      if constexpr (F8) {
+        float sa;                      // dequantisation scale of this row of the A operand
+        // layer 1 in FP32; h1 -> A (E4M3, row scale), silu'(z1) -> TMEM [H, 3H/2)
+        {
+          float m = 0.2785f;           // silu(z) >= -0.2785
+          for (int cc = 0; cc < C::kHalf; ++cc) {
+            const int col = c0 + cc;
+            float z = pb1[col];
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              float h0, d0, h1, d1;
-              silu_tc(v[i] + bias[col + i], h0, d0);
-              silu_tc(v[i + 1] + bias[col + i + 1], h1, d1);
-              if (layer == 2) {
-                const float w0 = pw5[col + i], w1 = pw5[col + i + 1];
-                tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
-                hp[i / 2] = pack_bf16(w0 * d0, w1 * d1);     // delta4
-              } else {
-                hp[i / 2] = pack_bf16(h0, h1);
-                dp[i / 2] = pack_bf16(d0, d1);
-              }
-            }
-            if (layer == 0) {
-              tmem_st16(lane_addr + H + C::kHalf + col / 2, dp);                 // silu'(z2)
-            } else if (layer == 1) {
+            for (int c = 0; c < 6; ++c) z = fmaf(pW1[col * 6 + c], x[c], z);
+            m = fmaxf(m, z);
+          }
+          const bool got = pair_max(m, xch, &xbar[g], xph, half, r, abort_flag, gerr);
+          if (!__all_sync(0xffffffffu, got)) break;
+          const float inv = 448.f / m;
+          sa = m / 448.f;
+          for (int cc = 0; cc < C::kHalf; cc += 32) {
+            const int col = c0 + cc;
+            uint32_t hq[8], dp[16];
 #pragma unroll
-              for (int q = 0; q < 4; ++q)                                         // silu'(z3)
-                *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8 * q)) =
-                    make_uint4(dp[4 * q], dp[4 * q + 1], dp[4 * q + 2], dp[4 * q + 3]);
-            }
-          } else {
-            // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
-            uint32_t dd[16];
-            if (layer == 3) {
+            for (int i = 0; i < 32; i += 4) {
+              float h[4], d[4];
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
-                const uint4 w4 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8 * q));
-                dd[4 * q] = w4.x; dd[4 * q + 1] = w4.y; dd[4 * q + 2] = w4.z; dd[4 * q + 3] = w4.w;
+                float z = pb1[col + i + q];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) z = fmaf(pW1[(col + i + q) * 6 + c], x[c], z);
+                silu_tc(z, h[q], d[q]);
               }
-            } else {
-              tmem_ld16(lane_addr + H + (layer == 4 ? C::kHalf : 0) + col / 2, dd);
-              tmem_wait_ld();
+              hq[i / 4] = pack_e4m3x4(h[0] * inv, h[1] * inv, h[2] * inv, h[3] * inv);
+              dp[i / 2] = pack_bf16(d[0], d[1]);
+              dp[i / 2 + 1] = pack_bf16(d[2], d[3]);
             }
-#pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              const float e0 = v[i] * bf16_lo(dd[i / 2]);
-              const float e1 = v[i + 1] * bf16_hi(dd[i / 2]);
-              if (layer == 5) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                  gpart[c] = fmaf(pW1[(col + i) * 6 + c], e0, fmaf(pW1[(col + i + 1) * 6 + c], e1, gpart[c]));
-              } else {
-                hp[i / 2] = pack_bf16(e0, e1);
-              }
-            }
+            *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
+            *reinterpret_cast<uint4*>(sA + a_off8(r, col + 16)) = make_uint4(hq[4], hq[5], hq[6], hq[7]);
+            tmem_st16(lane_addr + H + col / 2, dp);
           }
-          if (layer < 5) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
-                  make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-          }
-        }
-        if (layer == 0) tmem_wait_st();
-        if (layer < 5) {
+          tmem_wait_st();
           fence_async_smem();
           tc_before();
           mbar_arrive(a_ready);
+        }
+        for (int layer = 0; layer < 6; ++layer) {
+          const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
+          if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+          acc_phase ^= 1;
+          tc_after();
+          const float* sw = wsc + layer * H;
+          // bound of the row for the next A operand (layers 0, 1: silu(z); 3, 4: delta)
+          float inv = 0.f, sa_next = sa;
+          if (layer == 0 || layer == 1 || layer == 3 || layer == 4) {
+            const float* bias = pb + layer * H;
+            float m = layer <= 1 ? 0.2785f : 1e-30f;
+            for (int cc = 0; cc < C::kHalf; cc += 32) {
+              const int col = c0 + cc;
+              float v[32];
+              tmem_ld32(lane_addr + col, v);
+              tmem_wait_ld();
+              if (layer <= 1) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) m = fmaxf(m, fmaf(v[i], sa * sw[col + i], bias[col + i]));
+              } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) m = fmaxf(m, 1.1f * fabsf(v[i] * (sa * sw[col + i])));
+              }
+            }
+            const bool got2 = pair_max(m, xch, &xbar[g], xph, half, r, abort_flag, gerr);
+            if (!__all_sync(0xffffffffu, got2)) { ok = false; break; }
+            inv = 448.f / m;
+            sa_next = m / 448.f;
+          } else if (layer == 2) {
+            inv = 1.f / s4;
+            sa_next = s4;
+          }
+          for (int cc = 0; cc < C::kHalf; cc += 32) {
+            const int col = c0 + cc;
+            float v[32];
+            tmem_ld32(lane_addr + col, v);
+            tmem_wait_ld();
+            uint32_t hq[8], dp[16];
+            if (layer < 3) {
+              const float* bias = pb + layer * H;
+#pragma unroll
+              for (int i = 0; i < 32; i += 4) {
+                float h[4], d[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) silu_tc(fmaf(v[i + q], sa * sw[col + i + q], bias[col + i + q]), h[q], d[q]);
+                if (layer == 2) {
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) tpart = fmaf(pw5[col + i + q], h[q], tpart);
+                  hq[i / 4] = pack_e4m3x4(pw5[col + i] * d[0] * inv, pw5[col + i + 1] * d[1] * inv,
+                                          pw5[col + i + 2] * d[2] * inv, pw5[col + i + 3] * d[3] * inv);
+                } else {
+                  hq[i / 4] = pack_e4m3x4(h[0] * inv, h[1] * inv, h[2] * inv, h[3] * inv);
+                  dp[i / 2] = pack_bf16(d[0], d[1]);
+                  dp[i / 2 + 1] = pack_bf16(d[2], d[3]);
+                }
+              }
+              if (layer == 0) {
+                tmem_st16(lane_addr + H + C::kHalf + col / 2, dp);                 // silu'(z2)
+              } else if (layer == 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)                                         // silu'(z3)
+                  *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8 * q)) =
+                      make_uint4(dp[4 * q], dp[4 * q + 1], dp[4 * q + 2], dp[4 * q + 3]);
+              }
+            } else {
+              uint32_t dd[16];
+              if (layer == 3) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const uint4 w4 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8 * q));
+                  dd[4 * q] = w4.x; dd[4 * q + 1] = w4.y; dd[4 * q + 2] = w4.z; dd[4 * q + 3] = w4.w;
+                }
+              } else {
+                tmem_ld16(lane_addr + H + (layer == 4 ? C::kHalf : 0) + col / 2, dd);
+                tmem_wait_ld();
+              }
+              float e[32];
+#pragma unroll
+              for (int i = 0; i < 32; i += 2) {
+                e[i] = v[i] * (sa * sw[col + i]) * bf16_lo(dd[i / 2]);
+                e[i + 1] = v[i + 1] * (sa * sw[col + i + 1]) * bf16_hi(dd[i / 2]);
+              }
+              if (layer == 5) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+#pragma unroll
+                  for (int c = 0; c < 3; ++c) gpart[c] = fmaf(pW1[(col + i) * 6 + c], e[i], gpart[c]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < 32; i += 4)
+                  hq[i / 4] = pack_e4m3x4(e[i] * inv, e[i + 1] * inv, e[i + 2] * inv, e[i + 3] * inv);
+              }
+            }
+            if (layer < 5) {
+              *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
+              *reinterpret_cast<uint4*>(sA + a_off8(r, col + 16)) = make_uint4(hq[4], hq[5], hq[6], hq[7]);
+            }
+          }
+          sa = sa_next;
+          if (layer == 0) tmem_wait_st();
+          if (layer < 5) {
+            fence_async_smem();
+            tc_before();
+            mbar_arrive(a_ready);
+          }
+        }
+      } else {
+        // layer 1 in FP32: h1 -> A (BF16), silu'(z1) -> TMEM [H, 3H/2)
+        for (int cc = 0; cc < C::kHalf; cc += 32) {
+          const int col = c0 + cc;
+          uint32_t hp[16], dp[16];
+  #pragma unroll
+          for (int i = 0; i < 32; i += 2) {
+            float z0 = pb1[col + i], z1 = pb1[col + i + 1];
+  #pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              z0 = fmaf(pW1[(col + i) * 6 + c], x[c], z0);
+              z1 = fmaf(pW1[(col + i + 1) * 6 + c], x[c], z1);
+            }
+            float h0, d0, h1, d1;
+            silu_tc(z0, h0, d0);
+            silu_tc(z1, h1, d1);
+            hp[i / 2] = pack_bf16(h0, h1);
+            dp[i / 2] = pack_bf16(d0, d1);
+          }
+  #pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
+                make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+          tmem_st16(lane_addr + H + col / 2, dp);
+        }
+        tmem_wait_st();
+        fence_async_smem();
+        tc_before();
+        mbar_arrive(a_ready);
+
+        for (int layer = 0; layer < 6; ++layer) {
+          const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
+          if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+          acc_phase ^= 1;
+          tc_after();
+          for (int cc = 0; cc < C::kHalf; cc += 32) {
+            const int col = c0 + cc;
+            float v[32];
+            tmem_ld32(lane_addr + col, v);
+            tmem_wait_ld();
+            uint32_t hp[16], dp[16];
+            if (layer < 3) {
+              // forward layers 2..4
+              const float* bias = pb + layer * H;
+  #pragma unroll
+              for (int i = 0; i < 32; i += 2) {
+                float h0, d0, h1, d1;
+                silu_tc(v[i] + bias[col + i], h0, d0);
+                silu_tc(v[i + 1] + bias[col + i + 1], h1, d1);
+                if (layer == 2) {
+                  const float w0 = pw5[col + i], w1 = pw5[col + i + 1];
+                  tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
+                  hp[i / 2] = pack_bf16(w0 * d0, w1 * d1);     // delta4
+                } else {
+                  hp[i / 2] = pack_bf16(h0, h1);
+                  dp[i / 2] = pack_bf16(d0, d1);
+                }
+              }
+              if (layer == 0) {
+                tmem_st16(lane_addr + H + C::kHalf + col / 2, dp);                 // silu'(z2)
+              } else if (layer == 1) {
+  #pragma unroll
+                for (int q = 0; q < 4; ++q)                                         // silu'(z3)
+                  *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8 * q)) =
+                      make_uint4(dp[4 * q], dp[4 * q + 1], dp[4 * q + 2], dp[4 * q + 3]);
+              }
+            } else {
+              // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
+              uint32_t dd[16];
+              if (layer == 3) {
+  #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const uint4 w4 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8 * q));
+                  dd[4 * q] = w4.x; dd[4 * q + 1] = w4.y; dd[4 * q + 2] = w4.z; dd[4 * q + 3] = w4.w;
+                }
+              } else {
+                tmem_ld16(lane_addr + H + (layer == 4 ? C::kHalf : 0) + col / 2, dd);
+                tmem_wait_ld();
+              }
+  #pragma unroll
+              for (int i = 0; i < 32; i += 2) {
+                const float e0 = v[i] * bf16_lo(dd[i / 2]);
+                const float e1 = v[i + 1] * bf16_hi(dd[i / 2]);
+                if (layer == 5) {
+  #pragma unroll
+                  for (int c = 0; c < 3; ++c)
+                    gpart[c] = fmaf(pW1[(col + i) * 6 + c], e0, fmaf(pW1[(col + i + 1) * 6 + c], e1, gpart[c]));
+                } else {
+                  hp[i / 2] = pack_bf16(e0, e1);
+                }
+              }
+            }
+            if (layer < 5) {
+  #pragma unroll
+              for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
+                    make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+            }
+          }
+          if (layer == 0) tmem_wait_st();
+          if (layer < 5) {
+            fence_async_smem();
+            tc_before();
+            mbar_arrive(a_ready);
+          }
         }
       }
       if (!ok) break;
@@ -483,73 +693,108 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::kTmemCols));
 }
 
-// round-to-nearest-even FP32 -> BF16 on the host
-uint16_t to_bf16(float f) {
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  u += 0x7FFFu + ((u >> 16) & 1u);
-  return (uint16_t)(u >> 16);
-}
-
-template <int H>
+template <int H, bool F8>
 cudaError_t launch_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, cudaStream_t st) {
-  using C = Cfg<H>;
-  cudaError_t e = cudaFuncSetAttribute(k_tt_mlp_tc<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  using C = Cfg<H, F8>;
+  cudaError_t e = cudaFuncSetAttribute(k_tt_mlp_tc<H, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
-  k_tt_mlp_tc<H><<<num_sms, kTcThreads, C::kSmem, st>>>(net, src, out, (const uint8_t*)net.tc, net.err);
+  k_tt_mlp_tc<H, F8><<<num_sms, kTcThreads, C::kSmem, st>>>(net, src, out, (const uint8_t*)net.tc, net.err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool mlp_tc_supported(int H, int precision) {
-  return precision == SPIDER_BF16 && (H == 64 || H == 128 || H == 256);
+  if (precision == SPIDER_BF16) return H == 64 || H == 128 || H == 256;
+  if (precision == SPIDER_FP8) return H == 128 || H == 256;
+  return false;
 }
 
 // Weight images for the B operand, in the order the MMA consumes them:
 // W2, W3, W4 (forward: B[n][k] = W[n][k]) then W4^T, W3^T, W2^T (reverse:
-// B[n][k] = W[k][n]); each image is H/64 K-blocks of H rows x 128 bytes in
-// the 128-byte-swizzled K-major layout the shared-memory descriptor names.
-cudaError_t mlp_tc_prepare(const float* const Wn_host[3], int H, int precision, void** image, float** scales,
-                           cudaStream_t st) {
+// B[n][k] = W[k][n]); each image is K-blocks of H rows x 128 bytes (64 BF16 or
+// 128 E4M3 elements) in the 128-byte-swizzled K-major layout the shared-memory
+// descriptor names.  FP8: every row n of an image is divided by its scale
+// max_k |B[n][k]| / 448 before rounding; `scales` receives the 6 H column
+// scales followed by the scale of delta4, 1.1 max |w5| / 448.
+cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, int H, int precision,
+                           void** image, float** scales, cudaStream_t st) {
   *image = nullptr;
   *scales = nullptr;
   if (!mlp_tc_supported(H, precision)) return cudaErrorNotSupported;
-  const size_t img = (size_t)H * H * 2;
+  const bool f8 = precision == SPIDER_FP8;
+  const int eb = f8 ? 1 : 2, per_kb = 128 / eb;
+  const size_t img = (size_t)H * H * eb;
   std::vector<uint8_t> host(6 * img, 0);
+  std::vector<float> sc(f8 ? 6 * H + 1 : 0, 1.f);
   for (int l = 0; l < 6; ++l) {
     const float* W = Wn_host[l < 3 ? l : 5 - l];
     const bool transpose = l >= 3;
     uint8_t* base = host.data() + l * img;
-    for (int n = 0; n < H; ++n)
+    for (int n = 0; n < H; ++n) {
+      float inv = 1.f;
+      if (f8) {
+        float m = 0.f;
+        for (int k = 0; k < H; ++k) m = std::fmax(m, std::fabs(transpose ? W[(size_t)k * H + n] : W[(size_t)n * H + k]));
+        const float scale = m > 0.f ? m / 448.f : 1.f;
+        sc[(size_t)l * H + n] = scale;
+        inv = 1.f / scale;
+      }
       for (int k = 0; k < H; ++k) {
         const float v = transpose ? W[(size_t)k * H + n] : W[(size_t)n * H + k];
-        const int kb = k / 64, j = (k % 64) / 8;
+        const int kb = k / per_kb, j = (k % per_kb) / (16 / eb);
         const size_t off = (size_t)kb * H * 128 + (size_t)(n / 8) * 1024 + (size_t)(n % 8) * 128 +
-                           (size_t)((j ^ (n % 8)) * 16) + (size_t)(k % 8) * 2;
-        const uint16_t b = to_bf16(v);
-        std::memcpy(base + off, &b, 2);
+                           (size_t)((j ^ (n % 8)) * 16) + (size_t)(k % (16 / eb)) * eb;
+        if (f8) {
+          base[off] = to_e4m3(v * inv);
+        } else {
+          const uint16_t b = to_bf16(v);
+          std::memcpy(base + off, &b, 2);
+        }
       }
+    }
+  }
+  if (f8) {
+    float m = 0.f;
+    for (int i = 0; i < H; ++i) m = std::fmax(m, std::fabs(w5_host[i]));
+    sc[6 * H] = m > 0.f ? 1.1f * m / 448.f : 1.f;
   }
   void* d = nullptr;
+  float* ds = nullptr;
   cudaError_t e = cudaMalloc(&d, host.size());
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) {
+  if (f8 && (e = cudaMalloc(&ds, sc.size() * sizeof(float))) != cudaSuccess) {
     cudaFree(d);
     return e;
   }
+  e = cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && f8) e = cudaMemcpyAsync(ds, sc.data(), sc.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    if (ds) cudaFree(ds);
+    return e;
+  }
   *image = d;
+  *scales = ds;
   return cudaSuccess;
 }
 
 cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, cudaStream_t st) {
-  if (net.precision != SPIDER_BF16 || !net.tc || !net.err) return cudaErrorNotSupported;
+  if (!net.tc || !net.err) return cudaErrorNotSupported;
+  if (net.precision == SPIDER_FP8) {
+    if (!net.tc_scale) return cudaErrorNotSupported;
+    switch (net.H) {
+      case 128: return launch_tc<128, true>(net, src, out, num_sms, st);
+      case 256: return launch_tc<256, true>(net, src, out, num_sms, st);
+      default: return cudaErrorNotSupported;
+    }
+  }
+  if (net.precision != SPIDER_BF16) return cudaErrorNotSupported;
   switch (net.H) {
-    case 64: return launch_tc<64>(net, src, out, num_sms, st);
-    case 128: return launch_tc<128>(net, src, out, num_sms, st);
-    case 256: return launch_tc<256>(net, src, out, num_sms, st);
+    case 64: return launch_tc<64, false>(net, src, out, num_sms, st);
+    case 128: return launch_tc<128, false>(net, src, out, num_sms, st);
+    case 256: return launch_tc<256, false>(net, src, out, num_sms, st);
     default: return cudaErrorNotSupported;
   }
 }

@@ -638,6 +638,7 @@ constexpr int kDenseSlots = kDenseMax / 32;
 struct WarpSmem {
   int32_t mu[kCompMax];              // sorted members, padded to a power of two
   int32_t lrp[kCompMax + 1];         // local row pointers, padded
+  uint8_t perm[kCompMax];            // iterative path: rows by decreasing length
   union {
     struct {
       float vec[8][kCompMax];        // zh, zl, diag, res, y, p, Ap, dz (row starts while loading)
@@ -935,6 +936,16 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
     }
     // iterative path (row starts in dz while loading)
     warp_load_comp(v, off, n, n2, mu, S.lrp, reinterpret_cast<int32_t*>(dz), S.it.lcol, S.it.lsw, lane);
+    {
+      // row order by decreasing length, so that the lanes of a 32-row slot
+      // run inner loops of similar trip counts
+      int32_t* key = reinterpret_cast<int32_t*>(rs);
+      for (int i = lane; i < n2; i += 32) key[i] = i < n ? ((S.lrp[i + 1] - S.lrp[i]) << 8 | i) : -1;
+      __syncwarp();
+      warp_sort(key, n2, lane);
+      for (int r = lane; r < n; r += 32) S.perm[r] = (uint8_t)(key[n2 - 1 - r] & 255);
+      __syncwarp();
+    }
     for (int i = lane; i < n; i += 32) {
       zh[i] = 0.f;
       zl[i] = 0.f;
@@ -951,7 +962,8 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
     int it = 0;
     for (int round = 0; round < 8 && bb > 0.f && it < max_it; ++round) {
       float rz = 0.f, rr0 = 0.f;
-      for (int i = lane; i < n; i += 32) {
+      for (int r_ = lane; r_ < n; r_ += 32) {
+        const int i = S.perm[r_];
         const int32_t u = mu[i];
         float r;
         if (round == 0) {
@@ -984,7 +996,8 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
       bool first = true;
       while (it < max_it) {
         float dot = 0.f;
-        for (int i = lane; i < n; i += 32) {
+        for (int r_ = lane; r_ < n; r_ += 32) {
+          const int i = S.perm[r_];
           const float yu = yv[i];
           float sacc = 0.f;
           for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
@@ -1002,7 +1015,8 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
         const float alpha = pap > 0.f ? rz / pap : 0.f;
         float rzn = 0.f, rr = 0.f;
         __syncwarp();
-        for (int i = lane; i < n; i += 32) {
+        for (int r_ = lane; r_ < n; r_ += 32) {
+          const int i = S.perm[r_];
           dz[i] = fmaf(alpha, pv[i], dz[i]);
           const float r = fmaf(-alpha, ap[i], rs[i]);
           rs[i] = r;
@@ -1054,6 +1068,7 @@ struct CtaSmem {
   float vec[8][kCtaSm];             // zh, zl, diag, res, y, p, Ap, dz (row starts while loading)
   float lsw[kCtaSmEnt];
   uint16_t lcol[kCtaSmEnt];
+  uint16_t perm[kCtaSm];            // rows by decreasing length
 };
 static_assert(sizeof(CtaSmem) >= kCtaMax * sizeof(int32_t), "member sort buffer");
 
@@ -1118,6 +1133,13 @@ __device__ int cta_solve_smem(const StepView& v, CtaSmem& S, int32_t off, int n,
     S.lsw[e] = v.csr_sw[t];
     S.lcol[e] = (uint16_t)bsearch_le(mu, n2, v.csr_col[t]);
   }
+  {
+    int32_t* key = reinterpret_cast<int32_t*>(rs);
+    for (int i = tid; i < n2; i += nt) key[i] = i < n ? ((S.lrp[i + 1] - S.lrp[i]) << 10 | i) : -1;
+    __syncthreads();
+    cta_sort(key, n2);
+    for (int r = tid; r < n; r += nt) S.perm[r] = (uint16_t)(key[n2 - 1 - r] & 1023);
+  }
   __syncthreads();
   int par = 0;
   float bb = 0.f;
@@ -1133,7 +1155,8 @@ __device__ int cta_solve_smem(const StepView& v, CtaSmem& S, int32_t off, int n,
   int it = 0;
   for (int round = 0; round < 8 && bb > 0.f && it < max_it; ++round) {
     float rz = 0.f, rr0 = 0.f;
-    for (int i = tid; i < n; i += nt) {
+    for (int r_ = tid; r_ < n; r_ += nt) {
+      const int i = S.perm[r_];
       const int32_t u = mu[i];
       float r;
       if (round == 0) {
@@ -1165,7 +1188,8 @@ __device__ int cta_solve_smem(const StepView& v, CtaSmem& S, int32_t off, int n,
     bool first = true;
     while (it < max_it) {
       float dot = 0.f;
-      for (int i = tid; i < n; i += nt) {
+      for (int r_ = tid; r_ < n; r_ += nt) {
+        const int i = S.perm[r_];
         const float yu = yv[i];
         float sacc = 0.f;
         for (int l = S.lrp[i], l1 = S.lrp[i + 1]; l < l1; ++l) {
@@ -1182,7 +1206,8 @@ __device__ int cta_solve_smem(const StepView& v, CtaSmem& S, int32_t off, int n,
       const float pap = block_sum2(dot, 0.f, red2, par).x;
       const float alpha = pap > 0.f ? rz / pap : 0.f;
       float rzn = 0.f, rr = 0.f;
-      for (int i = tid; i < n; i += nt) {
+      for (int r_ = tid; r_ < n; r_ += nt) {
+        const int i = S.perm[r_];
         dz[i] = fmaf(alpha, pv[i], dz[i]);
         const float r = fmaf(-alpha, ap[i], rs[i]);
         rs[i] = r;

@@ -19,8 +19,8 @@ cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, 
                           cudaStream_t st);
 bool mlp_tc_supported(int H, int precision);
 // builds the tensor-core operand images of the hidden layers on the device
-cudaError_t mlp_tc_prepare(const float* const Wn_host[3], int H, int precision, void** image,
-                           float** scales, cudaStream_t st);
+cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, int H, int precision,
+                           void** image, float** scales, cudaStream_t st);
 
 // step (k_step.cu)
 cudaError_t configure_step_kernels(const StepView& v);

@@ -8,8 +8,12 @@ Jacobian for every touched pair, residuals, whitening solve, scatter, priors,
 Langevin update.  Inputs (the 3.2 GB catalog tables) are resident in HBM and far
 larger than L2; each step reads a fresh random 2% of them.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|fp8]
-                  [--impl ours|reference] [--workload 4|3|2|1]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8]
+                  [--impl ours|reference] [--workload 4|3|2|1|5] [--no-forms]
+
+The headline form is BF16 (tensor-core hidden layers); the FP32 and FP8 forms of
+the same step are timed on the same catalog afterwards and reported under
+"forms" (with the BF16 / FP32 ratio).
 
 --impl reference times the FP64 oracle (the CPU restatement of the method) on a
 bounded sample of the same workload on this host's cores.
@@ -171,6 +175,13 @@ def run_ours(args, rank, world):
         dist.all_reduce(ms, op=dist.ReduceOp.MAX)
     ms_dev, ms_total, e2e_ms = (float(x) for x in ms)
     ctx.close()
+    # the other precision forms on the same catalog (graph pass, same seeds)
+    forms = {}
+    if not args.no_forms:
+        for other in ("fp32", "bf16", "fp8"):
+            if other == args.precision:
+                continue
+            forms[other] = time_form(cat, other, eps, seed0, args, stream, world)
     if rank != 0:
         return None
     K = args.steps
@@ -212,11 +223,48 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * K / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": state_bytes,
                 "note": "spider_sgld_step (eps, seed passed by value) + spider_get_state per step"},
+        "forms": dict(forms, **({"bf16_over_fp32": steps_s / forms["fp32"]["value"]}
+                                if args.precision == "bf16" and "fp32" in forms else {})),
         "gpu_launches": launches_per_step(cat.spec.hyper.kappa > 0) * K,
         "clocks": clk,
         "setup_s": {"generate": t_gen, "create": t_create},
     }
     return line
+
+
+def time_form(cat, prec_name, eps, seed0, args, stream, world):
+    """Steps/s of another precision form of the same step on the same catalog:
+    warm-up, then K steps of the captured graph timed with CUDA events."""
+    import torch
+    from paper_2508_12117_gb300 import binding
+    prec = {"fp32": binding.FP32, "bf16": binding.BF16, "fp8": binding.FP8}[prec_name]
+    cfg = binding.config_for_catalog(cat, precision=prec, chain=0, thin=1, sample_cap=1)
+    ctx = binding.Context(cat.init_xyzt, cat.i, cat.j, cat.k, cat.dt, cat.stations,
+                          binding.net_for_catalog(cat), cfg, stream=stream.cuda_stream)
+    ctx.spider_set_timing(True)
+    for w in range(args.warmup):
+        ctx.spider_sgld_step(eps, seed0 + w)
+    mlp = 0.0
+    for s in range(args.steps):
+        ctx.spider_sgld_step(eps, seed0 + args.warmup + s)
+        mlp += ctx.spider_last_timing()["ms"][1]
+    ctx.spider_set_timing(False)
+    ctx.spider_sgld_step(eps, seed0 + 9_999)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for s in range(args.steps):
+        ctx.spider_sgld_step(eps, seed0 + 10_000 + s)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    ctx.close()
+    K = args.steps
+    return {"value": world * K / (float(ms[0]) * 1e-3), "unit": "steps/s",
+            "ms_per_step": float(ms[0]) / K, "travel_time_mlp_ms": mlp / K}
 
 
 # ---------------------------------------------------------------- batched
@@ -351,7 +399,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip timing the other precision forms on the same catalog")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -108,13 +108,33 @@ typedef struct {
   float pcg_tol;           /* whitening solve: target |u - A z| / |u|, with the
                               residual evaluated in double-float (refinement)     */
   int64_t sample_cap;      /* samples kept on the device (ring buffer)           */
+  /* update rule of spider_sgld_step (Sec. 3.2):
+   *   SPIDER_UPDATE_SGLD   theta += eps g + noise_scale sqrt(2 eps) eta
+   *   SPIDER_UPDATE_PSGLD  Eq. pSGLD: v = beta2 v + (1 - beta2) g*g,
+   *                        V = 1 / (sqrt(v) + upd_eps),
+   *                        theta += eps V g + noise_scale sqrt(2 eps V) eta
+   *   SPIDER_UPDATE_ADAM   stage 1 (Sec. 3.2): Adam on the log posterior (ascent),
+   *                        no noise: m = beta1 m + (1 - beta1) g, v as above,
+   *                        theta += eps (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + upd_eps),
+   *                        t = step counter + 1                                  */
+  int32_t update;
+  float beta1, beta2;      /* moment decay rates, in [0, 1)                       */
+  float upd_eps;           /* damping of the preconditioner (Sec. 4: 1e-5)        */
+  /* data term of the log posterior:
+   *   SPIDER_LOSS_WHITENED  Eq. marginal_sigma (Gaussian, whitened per station)
+   *   SPIDER_LOSS_L1        stage 1 (Sec. 3.2): -(N/n) sum_n |r_n|, no whitening */
+  int32_t loss;
 } spider_config;
+
+enum { SPIDER_UPDATE_SGLD = 0, SPIDER_UPDATE_PSGLD = 1, SPIDER_UPDATE_ADAM = 2 };
+enum { SPIDER_LOSS_WHITENED = 0, SPIDER_LOSS_L1 = 1 };
 
 typedef struct spider_ctx spider_ctx;
 
 /* Fills *cfg with the defaults: Table 1 / Sec. 4 values (kappa 0.03 s, p 0.25,
  * ell 40 km, centroid sigma 0.01), event prior 0.5 km / 0.1 s (Sec. 4.1),
- * full batch, blocks of 4096, FP32, thin 1, reorder 1, noise 1, whitening 1000 / 1e-7. */
+ * full batch, blocks of 4096, FP32, thin 1, reorder 1, noise 1, whitening 1000 / 1e-7,
+ * SGLD update (beta1 0.9, beta2 0.99, upd_eps 1e-5: Sec. 4), whitened loss. */
 void spider_config_default(spider_config *cfg);
 
 /* Validates and copies the catalog, stations and network; builds the canonical
@@ -164,6 +184,14 @@ int spider_get_state(spider_ctx *ctx, double *theta_out, int64_t *step_out);
 /* Replaces the state and step counter (exact resume: with the same per-step
  * seeds the continued chain is bit-identical).  Synchronous. */
 int spider_set_state(spider_ctx *ctx, const double *theta, int64_t step);
+
+/* Moment state of the pSGLD / Adam updates: m (first moment, Adam) and v
+ * (second moment), M x 4 FP64 each in caller order; either pointer may be NULL.
+ * Both start at zero; spider_set_state leaves them alone, so an exact resume of
+ * a pSGLD or Adam run restores both.  SPIDER_E_INVAL for the SGLD update (no
+ * moments are kept).  Synchronous. */
+int spider_get_moments(spider_ctx *ctx, double *m_out, double *v_out);
+int spider_set_moments(spider_ctx *ctx, const double *m, const double *v);
 
 /* Waits for queued device work; returns the first device-side error, if any. */
 int spider_sync(spider_ctx *ctx);

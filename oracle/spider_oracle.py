@@ -32,6 +32,18 @@ paper is silent or ambiguous the reading taken is stated in the docstring
   R8  canonical order: events renumbered by the Morton key of their initial
       positions (ties by index), observations sorted by (i, j, k) in the new
       numbering, ties by original index.
+  R9  stage 1 (Sec. 3.2, Eq. stage1loss with an L1 norm): the objective is
+      -(N/n) sum_n |r_n| plus the same event and centroid priors (they keep
+      the common translation of the catalog determined); d|r|/dr = sign(r),
+      0 at r = 0.
+  R10 pSGLD follows Eq. pSGLD as printed: v = beta2 v + (1 - beta2) g*g,
+      V = 1 / (sqrt(v) + eps_p), theta += eps V g + sqrt(2 eps V) eta (the
+      Gamma correction term of the original pSGLD paper is not printed and is
+      omitted); v starts at 0.
+  R11 the stage-1 optimiser is Adam with bias correction, t = 1, 2, ...:
+      m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g*g,
+      theta += eta (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps_p),
+      an ascent on the objective of R9.
 """
 from __future__ import annotations
 
@@ -416,7 +428,7 @@ def residuals(prob: Problem, theta, sel):
     return r, (ni, nj, nev, nst, T, dT)
 
 
-def log_posterior(prob: Problem, theta, sel=None, whiten="woodbury"):
+def log_posterior(prob: Problem, theta, sel=None, whiten="woodbury", loss="whitened"):
     """log p(theta | tau) up to constants (R7) and its gradient, for the
     observation subset `sel` (None = all) scaled by N / |sel| (Eq. sgd):
 
@@ -424,6 +436,7 @@ def log_posterior(prob: Problem, theta, sel=None, whiten="woodbury"):
           - 1/2 sum_m |(theta_m - mu_m) / sigma_e|^2        (event prior)
           - 1/2 |(mean(theta) - mean(theta_0)) / sigma_c|^2 (centroid prior, R1)
 
+    With loss="l1" the data term is -(N/n) sum_n |r_n| instead (R9).
     Returns (L, grad (M, 4), info dict)."""
     theta = np.asarray(theta, dtype=np.float64)
     M, N = prob.M, prob.N
@@ -432,9 +445,15 @@ def log_posterior(prob: Problem, theta, sel=None, whiten="woodbury"):
     n = sel.shape[0]
     scale = N / n if n else 0.0
     r, (ni, nj, nev, nst, T, dT) = residuals(prob, theta, sel)
-    fn = whiten_woodbury if whiten == "woodbury" else whiten_dense
-    q, quad = fn(r, prob.i[sel], prob.j[sel], prob.k[sel], prob.w[sel], prob.sigma,
-                 prob.kappa, prob.stations.shape[0])
+    if loss == "l1":
+        # -|r| has derivative -sign(r); in the notation below q = sign(r), and
+        # quad = 2 sum |r| so that -1/2 quad = -sum |r|
+        q = np.sign(r)
+        quad = 2.0 * float(np.abs(r).sum())
+    else:
+        fn = whiten_woodbury if whiten == "woodbury" else whiten_dense
+        q, quad = fn(r, prob.i[sel], prob.j[sel], prob.k[sel], prob.w[sel], prob.sigma,
+                     prob.kappa, prob.stations.shape[0])
     # d(-1/2 r^T Sigma^-1 r)/dT_p = sum_{n: p = (i_n,k_n)} q_n - sum_{n: p = (j_n,k_n)} q_n
     V = T.shape[0]
     s_node = np.bincount(ni, weights=q, minlength=V) - np.bincount(nj, weights=q, minlength=V)
@@ -483,6 +502,48 @@ def run_chain(prob: Problem, theta0, eps, seeds, noise_scale=1.0, thin=1,
         if callback is not None:
             callback(t, theta)
     return theta, samples
+
+
+# ---------------------------------------------------------------------------
+# pSGLD (Eq. pSGLD, R10) and the stage-1 Adam optimiser (Sec. 3.2, R11)
+# ---------------------------------------------------------------------------
+def psgld_update(theta, grad, v, eps, beta2, eps_p, noise, noise_scale=1.0):
+    """One pSGLD update; returns (theta', v')."""
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    V = 1.0 / (np.sqrt(v) + eps_p)
+    theta = theta + eps * V * grad + noise_scale * np.sqrt(2.0 * eps * V) * noise
+    return theta, v
+
+
+def adam_update(theta, grad, m, v, t, eta, beta1, beta2, eps_p):
+    """One Adam ascent step (t = 1, 2, ...); returns (theta', m', v')."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return theta + eta * mh / (np.sqrt(vh) + eps_p), m, v
+
+
+def run_updates(prob: Problem, theta0, eps, seeds, update="sgld", loss="whitened", beta1=0.9,
+                beta2=0.99, eps_p=1e-5, noise_scale=1.0, chain=0, catalog=0, m0=None, v0=None, t0=0):
+    """Iterate one update rule ("sgld", "psgld" or "adam") over the per-step
+    seeds (minibatch and noise keyed by the seed); t0 steps were taken before.
+    Returns (theta, m, v)."""
+    theta = np.array(theta0, dtype=np.float64)
+    m = np.zeros_like(theta) if m0 is None else np.array(m0, dtype=np.float64)
+    v = np.zeros_like(theta) if v0 is None else np.array(v0, dtype=np.float64)
+    for t, s in enumerate(seeds):
+        sel = None if (prob.batch_n <= 0 or prob.batch_n >= prob.N) else prob.batch(s)
+        _, g, _ = log_posterior(prob, theta, sel, loss=loss)
+        if update == "adam":
+            theta, m, v = adam_update(theta, g, m, v, t0 + t + 1, eps, beta1, beta2, eps_p)
+            continue
+        eta = langevin_noise(prob.M, s, chain, catalog)
+        if update == "psgld":
+            theta, v = psgld_update(theta, g, v, eps, beta2, eps_p, eta, noise_scale)
+        else:
+            theta = sgld_update(theta, g, eps, eta, noise_scale)
+    return theta, m, v
 
 
 def grad_norms(grad) -> np.ndarray:

@@ -21,6 +21,8 @@ SPIDER_OK = 0
 ERRORS = {-1: "INVAL", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "UNSUPPORTED"}
 TT_HOMOGENEOUS, TT_LINEAR_GRADIENT, TT_MLP = 0, 1, 2
 FP32, BF16, FP8 = 0, 1, 2
+UPDATE_SGLD, UPDATE_PSGLD, UPDATE_ADAM = 0, 1, 2
+LOSS_WHITENED, LOSS_L1 = 0, 1
 
 
 class SpiderError(RuntimeError):
@@ -50,7 +52,8 @@ class spider_config(C.Structure):
                 ("batch_n", C.c_int64), ("block_obs", C.c_int64), ("precision", C.c_int32),
                 ("thin", C.c_int32), ("reorder", C.c_int32), ("chain", C.c_int32),
                 ("catalog", C.c_int32), ("noise_scale", C.c_float), ("pcg_max_it", C.c_int32),
-                ("pcg_tol", C.c_float), ("sample_cap", C.c_int64)]
+                ("pcg_tol", C.c_float), ("sample_cap", C.c_int64), ("update", C.c_int32),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("upd_eps", C.c_float), ("loss", C.c_int32)]
 
 
 _lib = None
@@ -78,6 +81,8 @@ def load_library(path: str = LIB_PATH):
         "spider_samples": (C.c_int, [vp, pd, i64, pi64]),
         "spider_get_state": (C.c_int, [vp, pd, pi64]),
         "spider_set_state": (C.c_int, [vp, pd, i64]),
+        "spider_get_moments": (C.c_int, [vp, pd, pd]),
+        "spider_set_moments": (C.c_int, [vp, pd, pd]),
         "spider_sync": (C.c_int, [vp]),
         "spider_set_timing": (C.c_int, [vp, C.c_int]),
         "spider_last_timing": (C.c_int, [vp, pf, pi64, pi64, C.POINTER(i32)]),
@@ -275,6 +280,20 @@ class Context:
     def spider_set_state(self, theta, step: int):
         th = np.ascontiguousarray(theta, dtype=np.float64)
         _check(load_library().spider_set_state(self.h, _ptr(th, C.c_double), int(step)), self.h)
+
+    def spider_get_moments(self):
+        """(m, v) moment states of the pSGLD / Adam updates, M x 4 each."""
+        m = np.empty((self.M, 4), np.float64)
+        v = np.empty((self.M, 4), np.float64)
+        _check(load_library().spider_get_moments(self.h, _ptr(m, C.c_double), _ptr(v, C.c_double)), self.h)
+        return m, v
+
+    def spider_set_moments(self, m=None, v=None):
+        mm = None if m is None else np.ascontiguousarray(m, dtype=np.float64)
+        vv = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        _check(load_library().spider_set_moments(
+            self.h, _ptr(mm, C.c_double) if mm is not None else None,
+            _ptr(vv, C.c_double) if vv is not None else None), self.h)
 
     def spider_sync(self):
         _check(load_library().spider_sync(self.h), self.h)

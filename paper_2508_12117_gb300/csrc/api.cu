@@ -252,6 +252,11 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
   hp.full = full ? 1 : 0;
   hp.sample_slot = -1;
   if (mode == 1 && ((c->step + 1) % cfg.thin) == 0 && v.sample_cap > 0) hp.sample_slot = c->n_samples % v.sample_cap;
+  {
+    const double t = (double)(c->step + 1);
+    hp.bc1 = (float)(1.0 / (1.0 - std::pow((double)cfg.beta1, t)));
+    hp.bc2 = (float)(1.0 / (1.0 - std::pow((double)cfg.beta2, t)));
+  }
   if (c->timing) CK(c, cudaEventRecord(c->ev[0], st));
   CK(c, cudaMemcpyAsync(c->prm, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
   const bool graphable = mode == 1 && !c->timing && c->use_graph && c->graph_ok;
@@ -319,6 +324,11 @@ void spider_config_default(spider_config* c) {
   c->pcg_max_it = 1000;
   c->pcg_tol = 1e-7f;
   c->sample_cap = 16;
+  c->update = SPIDER_UPDATE_SGLD;
+  c->beta1 = 0.9f;
+  c->beta2 = 0.99f;
+  c->upd_eps = 1e-5f;
+  c->loss = SPIDER_LOSS_WHITENED;
 }
 
 }  // extern "C"
@@ -349,6 +359,12 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   if (c->cfg.thin < 1 || c->cfg.pcg_max_it < 0 || !(c->cfg.pcg_tol >= 0.f) || c->cfg.sample_cap < 0 ||
       !(c->cfg.noise_scale >= 0.f)) {
     c->err = "need thin >= 1, pcg_max_it >= 0, pcg_tol >= 0, sample_cap >= 0, noise_scale >= 0";
+    return bail(SPIDER_E_INVAL);
+  }
+  if (c->cfg.update < SPIDER_UPDATE_SGLD || c->cfg.update > SPIDER_UPDATE_ADAM ||
+      c->cfg.loss < SPIDER_LOSS_WHITENED || c->cfg.loss > SPIDER_LOSS_L1 || !(c->cfg.beta1 >= 0.f) ||
+      !(c->cfg.beta1 < 1.f) || !(c->cfg.beta2 >= 0.f) || !(c->cfg.beta2 < 1.f) || !(c->cfg.upd_eps > 0.f)) {
+    c->err = "need update in SPIDER_UPDATE_*, loss in SPIDER_LOSS_*, beta1, beta2 in [0, 1), upd_eps > 0";
     return bail(SPIDER_E_INVAL);
   }
   int rc = check_net(net, cfg->precision, &c->err);
@@ -530,6 +546,14 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   AL(dout, 8);
   const int64_t cap = c->cfg.sample_cap;
   AL(samples, (size_t)std::max<int64_t>(cap, 1) * M);
+  if (c->cfg.update != SPIDER_UPDATE_SGLD) {
+    AL(mom2, M);
+    if ((e = cudaMemsetAsync(v.mom2, 0, M * sizeof(float4), st))) return bail(cuda_fail(c, e, "memset"));
+  }
+  if (c->cfg.update == SPIDER_UPDATE_ADAM) {
+    AL(mom1, M);
+    if ((e = cudaMemsetAsync(v.mom1, 0, M * sizeof(float4), st))) return bail(cuda_fail(c, e, "memset"));
+  }
 #undef UP
 #undef AL
   v.sample_cap = cap;
@@ -539,7 +563,12 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   if ((e = cudaMemsetAsync(v.estamp, 0xFF, M * sizeof(int32_t), st))) return bail(cuda_fail(c, e, "memset"));
   if ((e = cudaMemsetAsync(v.counters, 0, kCntSlots * sizeof(int32_t), st))) return bail(cuda_fail(c, e, "memset"));
   const double s2 = cfg->sigma * cfg->sigma;
-  v.whiten = cfg->kappa > 0.0 ? 1 : 0;
+  v.whiten = (cfg->kappa > 0.0 && cfg->loss == SPIDER_LOSS_WHITENED) ? 1 : 0;
+  v.loss = cfg->loss;
+  v.update = cfg->update;
+  v.beta1 = cfg->beta1;
+  v.beta2 = cfg->beta2;
+  v.upd_eps = cfg->upd_eps;
   v.lam = v.whiten ? (float)(s2 / (cfg->kappa * cfg->kappa)) : 0.f;
   v.inv_s2 = (float)(1.0 / s2);
   v.inv_sig_e2 = make_float4((float)(1.0 / (cfg->sig_e[0] * cfg->sig_e[0])), (float)(1.0 / (cfg->sig_e[1] * cfg->sig_e[1])),
@@ -745,6 +774,52 @@ int spider_set_state(spider_ctx* c, const double* theta, int64_t step) {
   CK(c, cudaStreamSynchronize(c->stream));
   c->step = step;
   return SPIDER_OK;
+}
+
+static int moments_io(spider_ctx* c, double* m_out, double* v_out, const double* m_in, const double* v_in) {
+  if (!c) return SPIDER_E_INVAL;
+  if (c->cfg.update == SPIDER_UPDATE_SGLD) {
+    c->err = "the SGLD update keeps no moments";
+    return SPIDER_E_INVAL;
+  }
+  const size_t M = c->v.M;
+  float4* dev[2] = {c->v.mom1, c->v.mom2};
+  double* outs[2] = {m_out, v_out};
+  const double* ins[2] = {m_in, v_in};
+  std::vector<float4> buf(M);
+  for (int k = 0; k < 2; ++k) {
+    if (!dev[k]) continue;
+    if (outs[k]) {
+      CK(c, cudaMemcpyAsync(buf.data(), dev[k], M * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+      for (size_t m = 0; m < M; ++m) {
+        double* x = outs[k] + 4 * (size_t)c->ev_old[m];
+        x[0] = buf[m].x; x[1] = buf[m].y; x[2] = buf[m].z; x[3] = buf[m].w;
+      }
+    }
+    if (ins[k]) {
+      for (size_t m = 0; m < M; ++m) {
+        const double* x = ins[k] + 4 * (size_t)c->ev_old[m];
+        for (int a = 0; a < 4; ++a)
+          if (!std::isfinite(x[a]) || (k == 1 && x[a] < 0.0)) {
+            c->err = "moments must be finite (and the second moment non-negative)";
+            return SPIDER_E_INVAL;
+          }
+        buf[m] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+      }
+      CK(c, cudaMemcpyAsync(dev[k], buf.data(), M * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  return check_device_error(c);
+}
+
+int spider_get_moments(spider_ctx* c, double* m_out, double* v_out) {
+  return moments_io(c, m_out, v_out, nullptr, nullptr);
+}
+
+int spider_set_moments(spider_ctx* c, const double* m, const double* v) {
+  return moments_io(c, nullptr, nullptr, m, v);
 }
 
 int spider_sync(spider_ctx* c) {

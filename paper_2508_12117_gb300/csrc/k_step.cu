@@ -1523,11 +1523,19 @@ __global__ void k_final(StepView v) {
     const df32 d = df_add(df32{zh[li], zl[li]}, df32{-zh[lj], -zl[lj]});
     const df32 bz = df_mul_f(d, v.obs_sw[br.e0 + e]);
     const float r = v.r_obs[br.e0 + e];
-    const df32 t = df_add_f(df32{-bz.hi, -bz.lo}, r);
-    const float qe = v.inv_s2 * t.hi;
+    float qe;
+    if (v.loss == SPIDER_LOSS_L1) {
+      // stage 1: d(-sum |r|)/dr = -sign(r); the quadratic slot carries 2|r| so
+      // that the log posterior's -1/2 (quad) is -sum |r|
+      qe = r > 0.f ? 1.f : (r < 0.f ? -1.f : 0.f);
+      quad += 2.0 * fabs((double)r);
+    } else {
+      const df32 t = df_add_f(df32{-bz.hi, -bz.lo}, r);
+      qe = v.inv_s2 * t.hi;
+      quad += (double)r * (double)qe;
+    }
     qs[e] = qe;
     v.q_obs[br.e0 + e] = qe;
-    quad += (double)r * (double)qe;
   }
   quad = block_sum<double>(quad, smd);
   if (threadIdx.x == 0) v.dblk[s] = quad;
@@ -1637,15 +1645,49 @@ __global__ void k_event(StepView v) {
             (double)d.w * d.w * ise.w;
       if (!(isfinite(g.x) && isfinite(g.y) && isfinite(g.z) && isfinite(g.w))) bad = 1;
     } else {
-      const uint4 w = philox4x32_10(
-          make_uint4((uint32_t)v.ev_caller[m], (uint32_t)v.sub_chain[sb], (uint32_t)v.sub_catalog[sb], kTagNoise),
-          key);
-      const float2 n01 = box_muller(w.x, w.y), n23 = box_muller(w.z, w.w);
       float4 nd;
-      nd.x = d.x + eps * g.x + sq * n01.x;
-      nd.y = d.y + eps * g.y + sq * n01.y;
-      nd.z = d.z + eps * g.z + sq * n23.x;
-      nd.w = d.w + eps * g.w + sq * n23.y;
+      if (v.update == SPIDER_UPDATE_ADAM) {
+        // stage-1 optimiser: Adam ascent on the objective, no noise
+        float4 m1 = v.mom1[m], m2 = v.mom2[m];
+        const float b1 = v.beta1, b2 = v.beta2;
+        m1.x = fmaf(b1, m1.x, (1.f - b1) * g.x); m2.x = fmaf(b2, m2.x, (1.f - b2) * (g.x * g.x));
+        m1.y = fmaf(b1, m1.y, (1.f - b1) * g.y); m2.y = fmaf(b2, m2.y, (1.f - b2) * (g.y * g.y));
+        m1.z = fmaf(b1, m1.z, (1.f - b1) * g.z); m2.z = fmaf(b2, m2.z, (1.f - b2) * (g.z * g.z));
+        m1.w = fmaf(b1, m1.w, (1.f - b1) * g.w); m2.w = fmaf(b2, m2.w, (1.f - b2) * (g.w * g.w));
+        v.mom1[m] = m1;
+        v.mom2[m] = m2;
+        const float bc1 = pr.bc1, bc2 = pr.bc2, pe = v.upd_eps;
+        nd.x = d.x + eps * (m1.x * bc1) / (sqrtf(m2.x * bc2) + pe);
+        nd.y = d.y + eps * (m1.y * bc1) / (sqrtf(m2.y * bc2) + pe);
+        nd.z = d.z + eps * (m1.z * bc1) / (sqrtf(m2.z * bc2) + pe);
+        nd.w = d.w + eps * (m1.w * bc1) / (sqrtf(m2.w * bc2) + pe);
+      } else {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)v.ev_caller[m], (uint32_t)v.sub_chain[sb], (uint32_t)v.sub_catalog[sb], kTagNoise),
+            key);
+        const float2 n01 = box_muller(w.x, w.y), n23 = box_muller(w.z, w.w);
+        if (v.update == SPIDER_UPDATE_PSGLD) {
+          // Eq. pSGLD: per-coordinate preconditioner from the running second moment
+          float4 m2 = v.mom2[m];
+          const float b2 = v.beta2, pe = v.upd_eps, ns = pr.noise_scale;
+          m2.x = fmaf(b2, m2.x, (1.f - b2) * (g.x * g.x));
+          m2.y = fmaf(b2, m2.y, (1.f - b2) * (g.y * g.y));
+          m2.z = fmaf(b2, m2.z, (1.f - b2) * (g.z * g.z));
+          m2.w = fmaf(b2, m2.w, (1.f - b2) * (g.w * g.w));
+          v.mom2[m] = m2;
+          const float Vx = 1.f / (sqrtf(m2.x) + pe), Vy = 1.f / (sqrtf(m2.y) + pe);
+          const float Vz = 1.f / (sqrtf(m2.z) + pe), Vw = 1.f / (sqrtf(m2.w) + pe);
+          nd.x = d.x + eps * Vx * g.x + ns * sqrtf(2.f * eps * Vx) * n01.x;
+          nd.y = d.y + eps * Vy * g.y + ns * sqrtf(2.f * eps * Vy) * n01.y;
+          nd.z = d.z + eps * Vz * g.z + ns * sqrtf(2.f * eps * Vz) * n23.x;
+          nd.w = d.w + eps * Vw * g.w + ns * sqrtf(2.f * eps * Vw) * n23.y;
+        } else {
+          nd.x = d.x + eps * g.x + sq * n01.x;
+          nd.y = d.y + eps * g.y + sq * n01.y;
+          nd.z = d.z + eps * g.z + sq * n23.x;
+          nd.w = d.w + eps * g.w + sq * n23.y;
+        }
+      }
       if (!(isfinite(nd.x) && isfinite(nd.y) && isfinite(nd.z) && isfinite(nd.w))) bad = 1;
       v.dth[m] = nd;
       if (pr.sample_slot >= 0) v.samples[pr.sample_slot * v.M + m] = nd;

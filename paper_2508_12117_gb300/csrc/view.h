@@ -71,6 +71,7 @@ struct StepParams {
   int32_t full;          // 1: every block of every sub-problem
   int32_t pad;
   int64_t sample_slot;   // -1: no sample this step
+  float bc1, bc2;        // Adam bias corrections 1 / (1 - beta^t)
 };
 
 // Step state and tables.
@@ -176,11 +177,16 @@ struct StepView {
   double* dred;      // FP64 diagnostics partials, 4 x kMaxGrid
   double* dout;      // FP64 results: [0] loglik (scaled), [1] logprior, [2] logcen, [3] logpost
   float4* samples;
+  float4* mom1;      // Adam first moment (M), null otherwise
+  float4* mom2;      // pSGLD / Adam second moment (M), null for SGLD
   int64_t sample_cap;
   // constants
   float lam;        // sigma^2 / kappa^2
   float inv_s2;     // 1 / sigma^2
-  int whiten;       // kappa > 0
+  int whiten;       // kappa > 0 and the whitened loss
+  int loss;         // SPIDER_LOSS_*
+  int update;       // SPIDER_UPDATE_*
+  float beta1, beta2, upd_eps;
   float4 inv_sig_e2;   // 1 / sigma_e^2
   float4 inv_sig_c2;   // 1 / sigma_c^2
   int cen_grid;     // CTAs of the event kernel

@@ -388,3 +388,79 @@ def test_sgld_step_runs_and_is_deterministic():
     b, _ = O.run_chain(P, P.init, 1e-5, [5, 6, 7])
     c, _ = O.run_chain(P, P.init, 1e-5, [5, 6, 8])
     assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+# ---------------------------------------------------------------- stage 1, pSGLD, Adam
+def test_l1_objective_value_and_gradient():
+    # R9: the L1 data term is -(N/n) sum |r|; its gradient is checked against
+    # central differences (|r| is smooth away from r = 0, which a generic
+    # perturbed state avoids)
+    P = tiny_problem(M=8, S=3, K=3, seed=21)
+    rng = np.random.default_rng(21)
+    theta = P.init + np.c_[rng.normal(0, 0.2, (P.M, 3)), rng.normal(0, 0.05, P.M)]
+    L, g, info = O.log_posterior(P, theta, loss="l1")
+    r = O.residuals(P, theta, np.arange(P.N))[0]
+    assert np.abs(r).min() > 1e-4
+    assert abs(info["loglik"] + np.abs(r).sum()) < 1e-9 * np.abs(r).sum()
+    gf = np.zeros_like(theta)
+    h = (1e-6, 1e-6, 1e-6, 1e-7)
+    for m in range(P.M):
+        for a in range(4):
+            tp, tm = theta.copy(), theta.copy()
+            tp[m, a] += h[a]; tm[m, a] -= h[a]
+            gf[m, a] = (O.log_posterior(P, tp, loss="l1")[0] - O.log_posterior(P, tm, loss="l1")[0]) / (2 * h[a])
+    assert np.linalg.norm(g - gf) <= 1e-5 * np.linalg.norm(g)
+
+
+def test_adam_constant_gradient_closed_form():
+    # R11 with a constant gradient g: the bias-corrected moments are exactly g
+    # and g^2, so every step moves eta g / (|g| + eps_p)
+    g = np.array([[0.3, -2.0, 1e-3, 5.0]])
+    theta = np.zeros((1, 4)); m = np.zeros((1, 4)); v = np.zeros((1, 4))
+    eta, eps_p = 1e-3, 1e-5
+    for t in range(1, 41):
+        theta, m, v = O.adam_update(theta, g, m, v, t, eta, 0.9, 0.99, eps_p)
+    assert np.allclose(theta, 40 * eta * g / (np.abs(g) + eps_p), rtol=1e-12, atol=0)
+
+
+def test_adam_finds_the_map_of_a_gaussian():
+    # prior-only catalog (no observations): the log posterior is maximal at theta_0
+    P = tiny_problem(M=6, S=2, K=2, seed=22)
+    theta = P.init + 0.3
+    m = np.zeros_like(theta); v = np.zeros_like(theta)
+    for t in range(1, 3001):
+        g = -(theta - P.init) / P.sig_e ** 2
+        theta, m, v = O.adam_update(theta, g, m, v, t, 1e-2, 0.9, 0.99, 1e-8)
+    assert np.abs(theta - P.init).max() < 1e-3
+
+
+def test_psgld_constant_preconditioner_stationary_law():
+    # R10: with v frozen at c (the beta2 -> 1 limit) pSGLD is SGLD with step
+    # eps V, V = 1 / (sqrt(c) + eps_p): stationary law N(mu, 1 / (h (1 - eps V h / 2)))
+    h, mu, eps, c, eps_p = 4.0, -0.7, 0.05, 0.25, 1e-5
+    V = 1.0 / (np.sqrt(c) + eps_p)
+    C = 25_000
+    theta = np.full((C, 4), mu)
+    v = np.full((C, 4), c)
+    acc, acc2, n = 0.0, 0.0, 0
+    for t in range(1200):
+        g = -h * (theta - mu)
+        theta, v = O.psgld_update(theta, g, v, eps, 1.0, eps_p, O.langevin_noise(C, seed=5000 + t))
+        if t >= 200:
+            acc += theta.sum(); acc2 += (theta * theta).sum(); n += theta.size
+    mean = acc / n
+    var = acc2 / n - mean * mean
+    exact = 1.0 / (h * (1.0 - eps * V * h / 2.0))
+    assert abs(mean - mu) < 0.005
+    assert abs(var / exact - 1.0) < 0.01, (var, exact)
+
+
+def test_psgld_first_step_closed_form():
+    # from v = 0 the first update uses v = (1 - beta2) g^2
+    g = np.array([[1.0, -4.0, 0.5, 2.0]])
+    eta = np.array([[0.1, 0.2, -0.3, 0.4]])
+    eps, b2, eps_p = 1e-3, 0.99, 1e-5
+    th, v = O.psgld_update(np.zeros((1, 4)), g, np.zeros((1, 4)), eps, b2, eps_p, eta)
+    V = 1.0 / (np.sqrt(1 - b2) * np.abs(g) + eps_p)
+    assert np.allclose(th, eps * V * g + np.sqrt(2 * eps * V) * eta, rtol=1e-14, atol=0)
+    assert np.allclose(v, (1 - b2) * g * g, rtol=1e-15, atol=0)

@@ -193,6 +193,19 @@ int spider_set_state(spider_ctx *ctx, const double *theta, int64_t step);
 int spider_get_moments(spider_ctx *ctx, double *m_out, double *v_out);
 int spider_set_moments(spider_ctx *ctx, const double *m, const double *v);
 
+/* Stage-1 outlier rejection (Sec. 3.2: observations whose residual lies more
+ * than k_mad median absolute deviations from the median are discarded; the
+ * paper uses k_mad = 4).  Evaluates the residuals of every observation at the
+ * current state, then per catalog (sub-problem) the median of r and
+ * MAD = median |r - median| (an even count takes the mean of the two middle
+ * values; FP32 values, exact selection), and keep_n = |r_n - median| <= k_mad MAD.
+ * keep_out: host uint8[N] in the caller's observation order (1 = keep) or NULL;
+ * n_kept_out: count kept or NULL; med_out, mad_out: host double[n_sub] or NULL
+ * (n_sub = 1 for spider_create, catalogs x chains for spider_create_batch).
+ * Build the next stage's catalog from the kept observations.  Synchronous. */
+int spider_outlier_mask(spider_ctx *ctx, double k_mad, uint8_t *keep_out, int64_t *n_kept_out,
+                        double *med_out, double *mad_out);
+
 /* Waits for queued device work; returns the first device-side error, if any. */
 int spider_sync(spider_ctx *ctx);
 

@@ -44,6 +44,12 @@ paper is silent or ambiguous the reading taken is stated in the docstring
       m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g*g,
       theta += eta (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps_p),
       an ascent on the objective of R9.
+  R12 outlier rejection after stage 1 ("residuals greater than 4 median
+      absolute deviations", Sec. 3.2/4): an observation is kept when
+      |r - median(r)| <= 4 MAD with MAD = median |r - median(r)| (no
+      normal-consistency factor), per catalog, over all its observations at
+      the stage-1 solution; an even count takes the mean of the two middle
+      values.
 """
 from __future__ import annotations
 
@@ -544,6 +550,14 @@ def run_updates(prob: Problem, theta0, eps, seeds, update="sgld", loss="whitened
         else:
             theta = sgld_update(theta, g, eps, eta, noise_scale)
     return theta, m, v
+
+
+def mad_filter(r, k_mad=4.0):
+    """Outlier rejection of R12: (keep mask, median, MAD) of the residuals r."""
+    r = np.asarray(r, dtype=np.float64)
+    med = float(np.median(r))
+    mad = float(np.median(np.abs(r - med)))
+    return np.abs(r - med) <= k_mad * mad, med, mad
 
 
 def grad_norms(grad) -> np.ndarray:

@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "spider_set_state": (C.c_int, [vp, pd, i64]),
         "spider_get_moments": (C.c_int, [vp, pd, pd]),
         "spider_set_moments": (C.c_int, [vp, pd, pd]),
+        "spider_outlier_mask": (C.c_int, [vp, C.c_double, C.POINTER(C.c_uint8), pi64, pd, pd]),
         "spider_sync": (C.c_int, [vp]),
         "spider_set_timing": (C.c_int, [vp, C.c_int]),
         "spider_last_timing": (C.c_int, [vp, pf, pi64, pi64, C.POINTER(i32)]),
@@ -190,6 +191,7 @@ class Context:
             sta=np.ascontiguousarray(stations, dtype=np.float64))
         a = self._arrays
         self.M, self.N = a["xyzt0"].shape[0], a["i"].shape[0]
+        self.n_sub = 1
         cat = spider_catalog(self.M, self.N, _ptr(a["xyzt0"], C.c_double), _ptr(a["i"], C.c_int32),
                              _ptr(a["j"], C.c_int32), _ptr(a["k"], C.c_int32),
                              _ptr(a["dt"], C.c_double), None)
@@ -233,6 +235,7 @@ class Context:
         self.cfg = cfg
         self.M = sum(c.M for c in cats) * chains
         self.N = sum(c.N for c in cats) * chains
+        self.n_sub = len(cats) * chains
         self._arrays = None
         return self
 
@@ -294,6 +297,18 @@ class Context:
         _check(load_library().spider_set_moments(
             self.h, _ptr(mm, C.c_double) if mm is not None else None,
             _ptr(vv, C.c_double) if vv is not None else None), self.h)
+
+    def spider_outlier_mask(self, k_mad: float = 4.0):
+        """(keep mask over the caller's observations, median and MAD per sub-problem)."""
+        keep = np.empty(self.N, np.uint8)
+        kept = C.c_int64()
+        ns = self.n_sub
+        med = np.empty(ns, np.float64)
+        mad = np.empty(ns, np.float64)
+        _check(load_library().spider_outlier_mask(self.h, float(k_mad), _ptr(keep, C.c_uint8), C.byref(kept),
+                                                  _ptr(med, C.c_double), _ptr(mad, C.c_double)), self.h)
+        assert int(keep.sum()) == kept.value
+        return keep.astype(bool), med, mad
 
     def spider_sync(self):
         _check(load_library().spider_sync(self.h), self.h)

@@ -822,6 +822,42 @@ int spider_set_moments(spider_ctx* c, const double* m, const double* v) {
   return moments_io(c, nullptr, nullptr, m, v);
 }
 
+int spider_outlier_mask(spider_ctx* c, double k_mad, uint8_t* keep_out, int64_t* n_kept_out, double* med_out,
+                        double* mad_out) {
+  if (!c || !(k_mad > 0.0) || !std::isfinite(k_mad)) return SPIDER_E_INVAL;
+  int rc = evaluate(c, 0, 0, 0.f);          // full-batch residuals at the current state
+  if (rc) return rc;
+  rc = spider_sync(c);
+  if (rc) return rc;
+  const int ns = c->n_sub;
+  const size_t N = c->v.N;
+  void* scratch = nullptr;
+  uint8_t* keep = nullptr;
+  CK(c, cudaMallocAsync(&scratch, outlier_scratch_bytes(ns), c->stream));
+  cudaError_t e = cudaMallocAsync(&keep, N > 0 ? N : 1, c->stream);
+  std::vector<float> med(ns), mad(ns);
+  int64_t kept = 0;
+  if (e == cudaSuccess)
+    e = launch_outlier(c->v, ns, (float)k_mad, scratch, keep, c->num_sms, c->stream, med.data(), mad.data(), &kept);
+  std::vector<uint8_t> hk;
+  if (e == cudaSuccess && keep_out) {
+    hk.resize(N);
+    e = cudaMemcpyAsync(hk.data(), keep, N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  if (keep) cudaFreeAsync(keep, c->stream);
+  cudaFreeAsync(scratch, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "outlier mask");
+  if (keep_out)
+    for (size_t n = 0; n < N; ++n) keep_out[c->ord[n]] = hk[n];
+  if (n_kept_out) *n_kept_out = kept;
+  for (int i = 0; i < ns; ++i) {
+    if (med_out) med_out[i] = med[i];
+    if (mad_out) mad_out[i] = mad[i];
+  }
+  return check_device_error(c);
+}
+
 int spider_sync(spider_ctx* c) {
   if (!c) return SPIDER_E_INVAL;
   CK(c, cudaStreamSynchronize(c->stream));

@@ -32,6 +32,10 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
 cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, cudaStream_t st);
 cudaError_t launch_diag(const StepView& v, const float4* g, const float4* G, double* norms, double* part,
                         int grid, cudaStream_t st);
+// stage-1 outlier mask (k_outlier.cu)
+size_t outlier_scratch_bytes(int n_sub);
+cudaError_t launch_outlier(const StepView& v, int n_sub, float kmad, void* scratch, uint8_t* keep,
+                           int num_sms, cudaStream_t st, float* med_host, float* mad_host, int64_t* n_kept);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                 int64_t n, uint32_t* out, cudaStream_t st);
 

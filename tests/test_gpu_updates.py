@@ -114,3 +114,32 @@ def test_update_config_is_validated(cat1):
     for bad in (dict(update=7), dict(loss=3), dict(beta2=1.0), dict(beta1=-0.1), dict(upd_eps=0.0)):
         with pytest.raises(binding.SpiderError):
             binding.Context.from_catalog(cat1, **bad)
+
+
+def test_stage1_outlier_mask_matches_oracle():
+    # Laplace(0, 5 ms) noise + 2 % U(-0.5, 0.5) s outliers (the 100k-event recipe, scaled)
+    s = synth.scaled_spec(3, 4000, batch_n=1 << 16)
+    cat = synth.make_catalog(s)
+    ctx = binding.Context.from_catalog(cat, update=binding.UPDATE_ADAM, loss=binding.LOSS_L1)
+    for t in range(20):
+        ctx.spider_sgld_step(1e-3, 300 + t)
+    th, _ = ctx.spider_get_state()
+    keep, med, mad = ctx.spider_outlier_mask(4.0)
+    P = O.problem_from_catalog(cat)
+    r_caller = O.residuals(P, th, np.arange(P.N))[0]      # caller's observation order
+    ko, mo, ao = O.mad_filter(r_caller, 4.0)
+    near = np.abs(np.abs(r_caller - mo) - 4.0 * ao) < 1e-5
+    diff = keep != ko
+    print(f"stage-1 mask: N {P.N}, kept {keep.sum()} (oracle {ko.sum()}), median {med[0]*1e3:.4f} ms "
+          f"(oracle {mo*1e3:.4f}), MAD {mad[0]*1e3:.4f} ms (oracle {ao*1e3:.4f}), "
+          f"differing {diff.sum()} all near the cut: {bool((~near[diff]).sum() == 0)}")
+    assert abs(med[0] - mo) <= 2e-6 and abs(mad[0] - ao) <= 2e-6
+    assert not diff[~near].any()
+    # the next stage runs on the kept observations
+    nxt = binding.Context(th, cat.i[keep], cat.j[keep], cat.k[keep], cat.dt[keep], cat.stations,
+                          binding.net_for_catalog(cat),
+                          binding.config_for_catalog(cat, update=binding.UPDATE_PSGLD))
+    nxt.spider_sgld_step(2e-5, 1)
+    nxt.spider_sync()
+    nxt.close()
+    ctx.close()

@@ -464,3 +464,33 @@ def test_psgld_first_step_closed_form():
     V = 1.0 / (np.sqrt(1 - b2) * np.abs(g) + eps_p)
     assert np.allclose(th, eps * V * g + np.sqrt(2 * eps * V) * eta, rtol=1e-14, atol=0)
     assert np.allclose(v, (1 - b2) * g * g, rtol=1e-15, atol=0)
+
+
+def test_mad_filter_small_cases_by_hand():
+    keep, med, mad = O.mad_filter([3.0, 1.0, 2.0])
+    assert med == 2.0 and mad == 1.0 and keep.all()
+    # even count: median 2.5; deviations 1.5, 0.5, 0.5, 7.5 -> MAD 1.0; 10 lies 7.5 > 4 away
+    keep, med, mad = O.mad_filter([1.0, 2.0, 3.0, 10.0])
+    assert med == 2.5 and mad == 1.0 and keep.tolist() == [True, True, True, False]
+
+
+def test_mad_of_laplace_and_normal_samples():
+    rng = np.random.default_rng(30)
+    b, sd = 0.005, 0.005
+    _, med, mad = O.mad_filter(rng.laplace(0.0, b, 2_000_000))
+    assert abs(med) < 2e-5 and abs(mad / (b * np.log(2.0)) - 1.0) < 0.01      # Laplace MAD = b ln 2
+    _, med, mad = O.mad_filter(rng.normal(0.0, sd, 2_000_000))
+    assert abs(mad / (sd * 0.6744897501960817) - 1.0) < 0.01                    # normal MAD = 0.6745 sigma
+
+
+def test_mad_filter_rejects_gross_outliers():
+    rng = np.random.default_rng(31)
+    n = 500_000
+    r = rng.laplace(0.0, 0.005, n)
+    out = rng.random(n) < 0.02
+    r[out] = rng.uniform(-0.5, 0.5, out.sum())
+    keep, med, mad = O.mad_filter(r)
+    gross = out & (np.abs(r) > 0.05)
+    assert (~keep[gross]).mean() > 0.999
+    # Laplace inliers beyond the cut: P(|x - med| > 4 MAD) = exp(-4 MAD / b)
+    assert abs((~keep[~out]).mean() - np.exp(-4.0 * mad / 0.005)) < 0.003

@@ -206,6 +206,31 @@ int spider_set_moments(spider_ctx *ctx, const double *m, const double *v);
 int spider_outlier_mask(spider_ctx *ctx, double k_mad, uint8_t *keep_out, int64_t *n_kept_out,
                         double *med_out, double *mad_out);
 
+/* Linearisation-regime filter (Proposition 1, Eq. dd_linearization; Sec. 4
+ * keeps observations whose linearisation error is at most 5 %).  At the current
+ * state, observation (i, j, k) has dT = T(x_j, s_k) - T(x_i, s_k) and the
+ * linearised dT_lin = grad_x T(x_i, s_k) . (x_j - x_i); it is kept when
+ * |dT - dT_lin| <= max_rel |dT| (max_rel = 0.05 in the paper).  keep_out: host
+ * uint8[N] in the caller's observation order (1 = keep) or NULL; n_kept_out:
+ * count kept or NULL.  Build the next stage's catalog from the kept
+ * observations.  Synchronous. */
+int spider_linearisation_mask(spider_ctx *ctx, double max_rel, uint8_t *keep_out, int64_t *n_kept_out);
+
+/* Posterior summaries from the n stored samples (the ring of spider_samples,
+ * oldest first), per event and coordinate (x, y, z, t0):
+ *   median_out, halfwidth_out: the median and half the length of the interval
+ *     between the lo_pct and hi_pct percentiles (Sec. 3.5: e.g. [0.5, 99.5] for
+ *     a 99 % credible interval; linear interpolation between order statistics
+ *     at rank (n - 1) p / 100);
+ *   calib_out: the fraction of samples below the true value `truth` (Sec. 4.1
+ *     calibration; truth: host M x 4 FP64 caller order, or NULL);
+ *   ess_out: effective sample size (Sec. 5) n / tau, tau = 1 + 2 sum_{t >= 1}
+ *     rho_t over the lags while the autocorrelation rho_t stays positive.
+ * Outputs are host M x 4 FP64 in caller order, or NULL.  SPIDER_E_INVAL with
+ * fewer than 2 or more than 4096 stored samples.  Synchronous. */
+int spider_uq(spider_ctx *ctx, const double *truth, double lo_pct, double hi_pct, double *median_out,
+              double *halfwidth_out, double *calib_out, double *ess_out);
+
 /* Waits for queued device work; returns the first device-side error, if any. */
 int spider_sync(spider_ctx *ctx);
 

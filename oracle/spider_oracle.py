@@ -50,6 +50,16 @@ paper is silent or ambiguous the reading taken is stated in the docstring
       normal-consistency factor), per catalog, over all its observations at
       the stage-1 solution; an even count takes the mean of the two middle
       values.
+  R14 posterior summaries (Sec. 3.5, 4.1, 5): percentiles by linear
+      interpolation between order statistics at rank (n - 1) p / 100; the
+      credible half-width is half the [lo, hi] percentile interval; the
+      calibration value is the fraction of samples below the truth; the
+      effective sample size is n / tau with tau = 1 + 2 sum_t rho_t over the
+      lags t >= 1 while the sample autocorrelation rho_t stays positive.
+  R13 linearisation error (Proposition 1; Sec. 4 keeps observations whose
+      error is at most 5 %): for observation (i, j, k) the non-linear
+      difference dT = T(x_j, s_k) - T(x_i, s_k) and the linearised one
+      grad_x T(x_i, s_k) . (x_j - x_i); the error is relative to |dT|.
 """
 from __future__ import annotations
 
@@ -558,6 +568,49 @@ def mad_filter(r, k_mad=4.0):
     med = float(np.median(r))
     mad = float(np.median(np.abs(r - med)))
     return np.abs(r - med) <= k_mad * mad, med, mad
+
+
+def linearisation_filter(prob: Problem, theta, max_rel=0.05):
+    """Keep mask of R13 over all observations (caller order), and the relative
+    errors |dT - dT_lin| / |dT|."""
+    theta = np.asarray(theta, dtype=np.float64)
+    st = prob.stations[prob.k]
+    Ti, dTi = prob.model(theta[prob.i, :3], st)
+    Tj, _ = prob.model(theta[prob.j, :3], st)
+    dT = Tj - Ti
+    lin = (dTi * (theta[prob.j, :3] - theta[prob.i, :3])).sum(axis=1)
+    err = np.abs(dT - lin)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rel = err / np.abs(dT)
+    return err <= max_rel * np.abs(dT), rel
+
+
+def ess_series(x) -> float:
+    """Effective sample size of one chain (R14)."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    d = x - x.mean()
+    c0 = float((d * d).sum())
+    tau = 1.0
+    if c0 > 0.0:
+        for t in range(1, n):
+            rho = float((d[:-t] * d[t:]).sum()) / c0
+            if not rho > 0.0:
+                break
+            tau += 2.0 * rho
+    return n / tau
+
+
+def uq_stats(samples, truth=None, lo_pct=0.5, hi_pct=99.5):
+    """Per event and coordinate, from samples (n, M, 4) in time order: median,
+    credible half-width, calibration value (None without truth) and ESS (R14)."""
+    s = np.asarray(samples, dtype=np.float64)
+    med = np.percentile(s, 50.0, axis=0)
+    half = 0.5 * (np.percentile(s, hi_pct, axis=0) - np.percentile(s, lo_pct, axis=0))
+    calib = None if truth is None else (s < np.asarray(truth)[None]).mean(axis=0)
+    n, M, _ = s.shape
+    ess = np.array([[ess_series(s[:, m, a]) for a in range(4)] for m in range(M)])
+    return med, half, calib, ess
 
 
 def grad_norms(grad) -> np.ndarray:

@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH):
         "spider_get_moments": (C.c_int, [vp, pd, pd]),
         "spider_set_moments": (C.c_int, [vp, pd, pd]),
         "spider_outlier_mask": (C.c_int, [vp, C.c_double, C.POINTER(C.c_uint8), pi64, pd, pd]),
+        "spider_linearisation_mask": (C.c_int, [vp, C.c_double, C.POINTER(C.c_uint8), pi64]),
+        "spider_uq": (C.c_int, [vp, pd, C.c_double, C.c_double, pd, pd, pd, pd]),
         "spider_sync": (C.c_int, [vp]),
         "spider_set_timing": (C.c_int, [vp, C.c_int]),
         "spider_last_timing": (C.c_int, [vp, pf, pi64, pi64, C.POINTER(i32)]),
@@ -309,6 +311,25 @@ class Context:
                                                   _ptr(med, C.c_double), _ptr(mad, C.c_double)), self.h)
         assert int(keep.sum()) == kept.value
         return keep.astype(bool), med, mad
+
+    def spider_linearisation_mask(self, max_rel: float = 0.05):
+        """Keep mask over the caller's observations (linearisation error <= max_rel)."""
+        keep = np.empty(self.N, np.uint8)
+        kept = C.c_int64()
+        _check(load_library().spider_linearisation_mask(self.h, float(max_rel), _ptr(keep, C.c_uint8),
+                                                        C.byref(kept)), self.h)
+        assert int(keep.sum()) == kept.value
+        return keep.astype(bool)
+
+    def spider_uq(self, truth=None, lo_pct: float = 0.5, hi_pct: float = 99.5):
+        """Per event and coordinate: median, credible half-width, calibration
+        percentile of the truth (NaN without truth) and effective sample size."""
+        out = [np.empty((self.M, 4), np.float64) for _ in range(4)]
+        tr = None if truth is None else np.ascontiguousarray(truth, dtype=np.float64)
+        _check(load_library().spider_uq(self.h, _ptr(tr, C.c_double) if tr is not None else None,
+                                        float(lo_pct), float(hi_pct), *(_ptr(o, C.c_double) for o in out)),
+               self.h)
+        return dict(median=out[0], halfwidth=out[1], calib=out[2], ess=out[3])
 
     def spider_sync(self):
         _check(load_library().spider_sync(self.h), self.h)

@@ -858,6 +858,83 @@ int spider_outlier_mask(spider_ctx* c, double k_mad, uint8_t* keep_out, int64_t*
   return check_device_error(c);
 }
 
+int spider_linearisation_mask(spider_ctx* c, double max_rel, uint8_t* keep_out, int64_t* n_kept_out) {
+  if (!c || !(max_rel >= 0.0) || !std::isfinite(max_rel)) return SPIDER_E_INVAL;
+  int rc = evaluate(c, 0, 0, 0.f);          // T and dT/dx of every pair at the current state
+  if (rc) return rc;
+  rc = spider_sync(c);
+  if (rc) return rc;
+  const size_t N = c->v.N;
+  uint8_t* keep = nullptr;
+  unsigned long long* kept = nullptr;
+  CK(c, cudaMallocAsync(&kept, sizeof(unsigned long long), c->stream));
+  cudaError_t e = cudaMallocAsync(&keep, N > 0 ? N : 1, c->stream);
+  if (e == cudaSuccess) e = launch_linfilter(c->v, c->nb_full, (float)max_rel, keep, kept, c->stream);
+  std::vector<uint8_t> hk(keep_out ? N : 0);
+  unsigned long long kh = 0;
+  if (e == cudaSuccess && keep_out) e = cudaMemcpyAsync(hk.data(), keep, N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&kh, kept, sizeof(kh), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (keep) cudaFreeAsync(keep, c->stream);
+  cudaFreeAsync(kept, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "linearisation mask");
+  if (keep_out)
+    for (size_t n = 0; n < N; ++n) keep_out[c->ord[n]] = hk[n];
+  if (n_kept_out) *n_kept_out = (int64_t)kh;
+  return check_device_error(c);
+}
+
+int spider_uq(spider_ctx* c, const double* truth, double lo_pct, double hi_pct, double* median_out,
+              double* halfwidth_out, double* calib_out, double* ess_out) {
+  if (!c || !(lo_pct >= 0.0) || !(hi_pct <= 100.0) || !(lo_pct <= hi_pct)) return SPIDER_E_INVAL;
+  CK(c, cudaStreamSynchronize(c->stream));
+  int rc = check_device_error(c);
+  if (rc) return rc;
+  const int64_t have = std::min<int64_t>(c->n_samples, c->v.sample_cap);
+  if (have < 2 || have > uq_max_samples()) {
+    c->err = "spider_uq needs 2..4096 stored samples";
+    return SPIDER_E_INVAL;
+  }
+  const int64_t first = c->n_samples - have;
+  const size_t M = c->v.M;
+  std::vector<double> toff;
+  if (truth) {
+    toff.resize(4 * M);
+    for (size_t m = 0; m < M; ++m)
+      for (int a = 0; a < 4; ++a) toff[4 * m + a] = truth[4 * (size_t)c->ev_old[m] + a] - c->th0[4 * m + a];
+  }
+  double* d = nullptr;
+  const size_t nb = 4 * M * sizeof(double);
+  CK(c, cudaMallocAsync(&d, 5 * nb, c->stream));
+  double* dt = d;
+  double* outs[4] = {d + 4 * M, d + 8 * M, d + 12 * M, d + 16 * M};
+  double* want[4] = {median_out, halfwidth_out, calib_out, ess_out};
+  cudaError_t e = cudaSuccess;
+  if (truth) e = cudaMemcpyAsync(dt, toff.data(), nb, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = launch_uq(c->v, first % c->v.sample_cap, (int)have, truth ? dt : nullptr, lo_pct, hi_pct,
+                  want[0] ? outs[0] : nullptr, want[1] ? outs[1] : nullptr, truth && want[2] ? outs[2] : nullptr,
+                  want[3] ? outs[3] : nullptr, c->stream);
+  std::vector<double> h(4 * M);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    if (!want[k] || (k == 2 && !truth)) continue;
+    e = cudaMemcpyAsync(h.data(), outs[k], nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) break;
+    for (size_t m = 0; m < M; ++m)
+      for (int a = 0; a < 4; ++a) {
+        double val = h[4 * m + a];
+        if (k == 0) val += c->th0[4 * m + a];          // the median back to absolute coordinates
+        want[k][4 * (size_t)c->ev_old[m] + a] = val;
+      }
+  }
+  cudaFreeAsync(d, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "posterior summaries");
+  if (calib_out && !truth)
+    for (size_t i = 0; i < 4 * M; ++i) calib_out[i] = std::nan("");
+  return check_device_error(c);
+}
+
 int spider_sync(spider_ctx* c) {
   if (!c) return SPIDER_E_INVAL;
   CK(c, cudaStreamSynchronize(c->stream));

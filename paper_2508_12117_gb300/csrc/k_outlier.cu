@@ -9,6 +9,7 @@
 
 #include <cstdint>
 
+#include "dfloat.cuh"
 #include "kernels.h"
 #include "spider.h"
 #include "view.h"
@@ -189,6 +190,62 @@ cudaError_t launch_outlier(const StepView& v, int n_sub, float kmad, void* scrat
   if ((e = cudaStreamSynchronize(st))) return e;
   *n_kept = (int64_t)kh;
   return cudaSuccess;
+}
+
+}  // namespace spider
+
+// ---------------------------------------------------------------------------
+// Linearisation-regime filter (Proposition 1; Sec. 4 drops observations whose
+// linearisation error exceeds 5 %): with T and dT/dx_s of every pair at the
+// current state, observation (i, j, k) has
+//   dT = T(x_j, s_k) - T(x_i, s_k),   dT_lin = grad_x T(x_i, s_k) . (x_j - x_i),
+// and is kept when |dT - dT_lin| <= max_rel |dT|.
+namespace spider {
+namespace {
+
+__global__ void k_linfilter(StepView v, float max_rel, uint8_t* keep, unsigned long long* kept) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const int s = blockIdx.x;
+  const int32_t b = v.sel[s];
+  const int32_t q0 = v.blk_node_off[b];
+  const int64_t e0 = v.blk_e0[b];
+  const int ne = v.blk_e0[b + 1] - v.blk_e0[b];
+  int mine = 0;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const uint32_t lij = v.obs_l[e0 + e];
+    const int32_t qi = q0 + (int)(lij & 0xFFFF), qj = q0 + (int)(lij >> 16);
+    const int32_t ui = v.loc2u[qi], uj = v.loc2u[qj];
+    const float2 ti = v.T2[ui], tj = v.T2[uj];
+    const float4 Ji = v.J[ui];
+    const int32_t mi = v.pair_ev[v.node_pair[qi]], mj = v.pair_ev[v.node_pair[qj]];
+    const float4 hi_i = v.th0_hi[mi], lo_i = v.th0_lo[mi], d_i = v.dth[mi];
+    const float4 hi_j = v.th0_hi[mj], lo_j = v.th0_lo[mj], d_j = v.dth[mj];
+    const df32 dT = df_add(df32{tj.x, tj.y}, df32{-ti.x, -ti.y});
+    const float dx = df_coord_diff(hi_j.x, lo_j.x, d_j.x - d_i.x, hi_i.x, lo_i.x).hi;
+    const float dy = df_coord_diff(hi_j.y, lo_j.y, d_j.y - d_i.y, hi_i.y, lo_i.y).hi;
+    const float dz = df_coord_diff(hi_j.z, lo_j.z, d_j.z - d_i.z, hi_i.z, lo_i.z).hi;
+    const float lin = fmaf(Ji.x, dx, fmaf(Ji.y, dy, Ji.z * dz));
+    const float err = fabsf(df_add_f(dT, -lin).hi);
+    const uint8_t k = err <= max_rel * fabsf(dT.hi) ? 1 : 0;
+    keep[e0 + e] = k;
+    mine += k;
+  }
+  atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(kept, (unsigned long long)cnt);
+}
+
+}  // namespace
+
+// after a full-batch evaluation (every block selected, T and J per unique pair)
+cudaError_t launch_linfilter(const StepView& v, int64_t n_b, float max_rel, uint8_t* keep,
+                             unsigned long long* kept, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(kept, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (n_b > 0) k_linfilter<<<(unsigned)n_b, 256, 0, st>>>(v, max_rel, keep, kept);
+  return cudaGetLastError();
 }
 
 }  // namespace spider

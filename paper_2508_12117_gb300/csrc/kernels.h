@@ -36,6 +36,12 @@ cudaError_t launch_diag(const StepView& v, const float4* g, const float4* G, dou
 size_t outlier_scratch_bytes(int n_sub);
 cudaError_t launch_outlier(const StepView& v, int n_sub, float kmad, void* scratch, uint8_t* keep,
                            int num_sms, cudaStream_t st, float* med_host, float* mad_host, int64_t* n_kept);
+cudaError_t launch_linfilter(const StepView& v, int64_t n_b, float max_rel, uint8_t* keep,
+                             unsigned long long* kept, cudaStream_t st);
+// posterior summaries (k_uq.cu)
+int uq_max_samples();
+cudaError_t launch_uq(const StepView& v, int64_t first, int n, const double* truth_off, double lo_pct,
+                      double hi_pct, double* med, double* half, double* calib, double* ess, cudaStream_t st);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                 int64_t n, uint32_t* out, cudaStream_t st);
 

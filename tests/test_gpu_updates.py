@@ -143,3 +143,44 @@ def test_stage1_outlier_mask_matches_oracle():
     nxt.spider_sync()
     nxt.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("wid", [1, 2])
+def test_linearisation_mask_matches_oracle(wid):
+    cat = synth.make_catalog(wid)
+    ctx = binding.Context.from_catalog(cat)
+    rng = np.random.default_rng(wid)
+    theta = cat.init_xyzt + np.c_[rng.normal(0, 0.1, (cat.M, 3)), np.zeros(cat.M)]
+    ctx.spider_set_state(theta, 0)
+    keep = ctx.spider_linearisation_mask(0.05)
+    P = O.problem_from_catalog(cat)
+    ko, rel = O.linearisation_filter(P, theta, 0.05)
+    st = P.stations[P.k]
+    dT = np.abs(P.model(theta[P.j, :3], st)[0] - P.model(theta[P.i, :3], st)[0])
+    near = np.abs(rel * dT - 0.05 * dT) <= 3e-6          # within the FP32 travel-time accuracy of the cut
+    diff = keep != ko
+    print(f"workload {wid}: kept {keep.sum()} of {P.N} (oracle {ko.sum()}), differing {diff.sum()}, "
+          f"all near the cut: {bool(not diff[~near].any())}")
+    assert not diff[~near].any()
+    ctx.close()
+
+
+def test_uq_summaries_match_oracle(cat1):
+    eps = cat1.spec.hyper.eps
+    ctx = binding.Context.from_catalog(cat1, thin=2, sample_cap=300)
+    for t in range(600):
+        ctx.spider_sgld_step(eps, 40_000 + t)
+    samples = ctx.spider_samples(300)
+    uq = ctx.spider_uq(cat1.true_xyzt, 0.5, 99.5)
+    med, half, calib, ess = O.uq_stats(samples, cat1.true_xyzt, 0.5, 99.5)
+    print(f"UQ over {samples.shape[0]} samples: median |d| {np.abs(uq['median'] - med).max():.2e} km, "
+          f"half-width |d| {np.abs(uq['halfwidth'] - half).max():.2e} km, ESS rel "
+          f"{np.abs(uq['ess'] / ess - 1).max():.2e}, mean half-width x {half[:, 0].mean() * 1e3:.1f} m, "
+          f"median ESS {np.median(ess):.1f}")
+    assert np.abs(uq["median"] - med).max() <= 1e-9
+    assert np.abs(uq["halfwidth"] - half).max() <= 1e-9
+    assert np.array_equal(uq["calib"], calib)
+    assert np.abs(uq["ess"] / ess - 1).max() <= 1e-9
+    nt = ctx.spider_uq(None)
+    assert np.isnan(nt["calib"]).all()
+    ctx.close()

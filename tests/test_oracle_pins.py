@@ -494,3 +494,64 @@ def test_mad_filter_rejects_gross_outliers():
     assert (~keep[gross]).mean() > 0.999
     # Laplace inliers beyond the cut: P(|x - med| > 4 MAD) = exp(-4 MAD / b)
     assert abs((~keep[~out]).mean() - np.exp(-4.0 * mad / 0.005)) < 0.003
+
+
+def test_linearisation_error_closed_forms():
+    # homogeneous medium, c = 6 km/s, station at the origin, event i at distance r
+    c = 6.0
+    model = O.Model("homogeneous", v0=c)
+    st = np.zeros((1, 3))
+    xi = np.array([3.0, 4.0, 12.0])                 # r = 13
+    n = xi / np.linalg.norm(xi)
+    perp = np.cross(n, [0.0, 0.0, 1.0]); perp /= np.linalg.norm(perp)
+    cases = [xi + 0.8 * n, xi + 0.8 * perp, xi + np.array([0.01, -0.02, 0.015])]
+    init = np.vstack([np.r_[xi, 0.0]] + [np.r_[x, 0.0] for x in cases])
+    P = O.Problem(init, st, np.zeros(3, int), np.arange(1, 4), np.zeros(3, int), np.zeros(3), model,
+                  0.01, 0.0, 0.25, 40.0, 1e-5, np.ones(4), np.ones(4))
+    keep, rel = O.linearisation_filter(P, init, 0.05)
+    r = np.linalg.norm(xi)
+    # along the ray the travel time is linear: no error
+    assert rel[0] < 1e-12 and keep[0]
+    # across the ray dT = (sqrt(r^2 + d^2) - r) / c and the linear term vanishes: error 100 %
+    assert abs(rel[1] - 1.0) < 1e-9 and not keep[1]
+    # small generic offsets: the error is the Hessian term 1/2 dx^T (I - n n^T) dx / (c r) + O(dx^3)
+    dx = cases[2] - xi
+    H = (np.eye(3) - np.outer(n, n)) / (c * r)
+    dT = (np.linalg.norm(cases[2]) - r) / c
+    assert abs(rel[2] * abs(dT) - 0.5 * dx @ H @ dx) < 1e-3 * 0.5 * dx @ H @ dx + 1e-12
+
+
+def test_percentiles_and_halfwidth_by_hand():
+    # 4 samples 1, 2, 3, 4 (one event, one coordinate): ranks (n - 1) p / 100
+    s = np.zeros((4, 1, 4)); s[:, 0, 0] = [4.0, 1.0, 3.0, 2.0]
+    med, half, _, _ = O.uq_stats(s, lo_pct=0.5, hi_pct=99.5)
+    assert med[0, 0] == 2.5
+    lo, hi = 1.0 + 0.015, 4.0 - 0.015                    # ranks 0.015 and 2.985
+    assert abs(half[0, 0] - 0.5 * (hi - lo)) < 1e-12
+
+
+def test_ess_of_ar1_chains():
+    # AR(1) x_t = phi x_{t-1} + e_t has integrated time (1 + phi) / (1 - phi)
+    rng = np.random.default_rng(40)
+    n = 40_000
+    for phi in (0.0, 0.5, 0.8):
+        e = rng.normal(size=n)
+        x = np.empty(n); x[0] = e[0] / np.sqrt(1 - phi * phi)
+        for t in range(1, n):
+            x[t] = phi * x[t - 1] + e[t]
+        want = n * (1 - phi) / (1 + phi)
+        assert abs(O.ess_series(x) / want - 1.0) < 0.1, (phi, O.ess_series(x), want)
+
+
+def test_calibration_of_an_exact_posterior_is_uniform():
+    # truth and samples drawn from the same law: the calibration values are uniform
+    rng = np.random.default_rng(41)
+    M, n = 1000, 100
+    mu = rng.normal(size=(M, 4))
+    truth = mu + rng.normal(size=(M, 4))
+    samples = mu[None] + rng.normal(size=(n, M, 4))
+    _, _, calib, ess = O.uq_stats(samples, truth)
+    c = calib.ravel()
+    assert abs(c.mean() - 0.5) < 0.01 and abs(c.var() - 1 / 12) < 0.005
+    # independent draws: ESS close to n
+    assert abs(np.median(ess) / n - 1.0) < 0.15

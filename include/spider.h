@@ -191,6 +191,11 @@ int spider_set_state(spider_ctx *ctx, const double *theta, int64_t step);
  * a pSGLD or Adam run restores both.  SPIDER_E_INVAL for the SGLD update (no
  * moments are kept).  Synchronous. */
 int spider_get_moments(spider_ctx *ctx, double *m_out, double *v_out);
+
+/* Sets the multiplier of the injected noise for the following steps (Sec. 3.2:
+ * stage 2 runs with the noise off, stage 3 ramps it linearly to full
+ * amplitude).  noise_scale >= 0.  Takes effect at the next spider_sgld_step. */
+int spider_set_noise_scale(spider_ctx *ctx, float noise_scale);
 int spider_set_moments(spider_ctx *ctx, const double *m, const double *v);
 
 /* Stage-1 outlier rejection (Sec. 3.2: observations whose residual lies more

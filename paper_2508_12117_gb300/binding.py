@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "spider_get_state": (C.c_int, [vp, pd, pi64]),
         "spider_set_state": (C.c_int, [vp, pd, i64]),
         "spider_get_moments": (C.c_int, [vp, pd, pd]),
+        "spider_set_noise_scale": (C.c_int, [vp, f32]),
         "spider_set_moments": (C.c_int, [vp, pd, pd]),
         "spider_outlier_mask": (C.c_int, [vp, C.c_double, C.POINTER(C.c_uint8), pi64, pd, pd]),
         "spider_linearisation_mask": (C.c_int, [vp, C.c_double, C.POINTER(C.c_uint8), pi64]),
@@ -285,6 +286,9 @@ class Context:
     def spider_set_state(self, theta, step: int):
         th = np.ascontiguousarray(theta, dtype=np.float64)
         _check(load_library().spider_set_state(self.h, _ptr(th, C.c_double), int(step)), self.h)
+
+    def spider_set_noise_scale(self, scale: float):
+        _check(load_library().spider_set_noise_scale(self.h, float(scale)), self.h)
 
     def spider_get_moments(self):
         """(m, v) moment states of the pSGLD / Adam updates, M x 4 each."""

@@ -814,6 +814,12 @@ static int moments_io(spider_ctx* c, double* m_out, double* v_out, const double*
   return check_device_error(c);
 }
 
+int spider_set_noise_scale(spider_ctx* c, float noise_scale) {
+  if (!c || !(noise_scale >= 0.f) || !std::isfinite(noise_scale)) return SPIDER_E_INVAL;
+  c->cfg.noise_scale = noise_scale;
+  return SPIDER_OK;
+}
+
 int spider_get_moments(spider_ctx* c, double* m_out, double* v_out) {
   return moments_io(c, m_out, v_out, nullptr, nullptr);
 }

@@ -184,3 +184,24 @@ def test_uq_summaries_match_oracle(cat1):
     nt = ctx.spider_uq(None)
     assert np.isnan(nt["calib"]).all()
     ctx.close()
+
+
+def test_noise_ramp_matches_oracle(cat1):
+    # stage 2 (noise off) then stage 3 (linear ramp to full amplitude), pSGLD
+    eps = 2e-5
+    ctx = binding.Context.from_catalog(cat1, update=binding.UPDATE_PSGLD)
+    P = O.problem_from_catalog(cat1)
+    theta, m, v = cat1.init_xyzt, None, None
+    schedule = [0.0] * 20 + [k / 20 for k in range(1, 21)]
+    for t, ns in enumerate(schedule):
+        ctx.spider_set_noise_scale(ns)
+        ctx.spider_sgld_step(eps, 60_000 + t)
+        theta, m, v = O.run_updates(P, theta, eps, [60_000 + t], update="psgld", noise_scale=ns,
+                                    m0=m, v0=v, t0=t)
+    th, _ = ctx.spider_get_state()
+    dx_m = np.abs(th[:, :3] - theta[:, :3]).max() * 1e3
+    print(f"noise ramp, {len(schedule)} steps: max |dx| {dx_m:.4f} m")
+    assert dx_m <= 1.0
+    with pytest.raises(binding.SpiderError):
+        ctx.spider_set_noise_scale(-1.0)
+    ctx.close()

@@ -8,12 +8,12 @@
 //       delta4 = w5 * silu'(z4);  delta_{l-1} = (W_l^T delta_l) * silu'(z_{l-1})
 //   dtau/dx = W1[:, :3]^T delta1 (FP32),  dT/dx = tau (x - s)/r + r dtau/dx.
 //
-// One CTA per SM, persistent over tiles; 10 warps:
-//   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one pair per
-//              lane) and columns [ (w / 4) H/2, (w / 4 + 1) H/2 );
-//   warp 8     producer: 1-D bulk async copies (cp.async.bulk) of pre-swizzled
+// One CTA per SM, persistent over tiles; 18 warps:
+//   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one pair per
+//              lane) and columns [ (w / 4) H/4, (w / 4 + 1) H/4 ), 16 at a time;
+//   warp 16    producer: 1-D bulk async copies (cp.async.bulk) of pre-swizzled
 //              weight K-blocks (H rows x 64 BF16) into a two-stage ring;
-//   warp 9     MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = H,
+//   warp 17    MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = H,
 //              K = 16, A = activations (SW128 K-major, shared memory),
 //              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
 // TMEM (2H columns): [0, H) accumulator, [H, 3H/2) silu'(z1) and [3H/2, 2H)
@@ -21,8 +21,8 @@
 // FP8 form (kind::f8f6f4, E4M3 operands, FP32 accumulation): the weight images
 // carry one scale per output column (max |W| / 448); each activation row is
 // quantised with its own scale, from a first pass over the accumulator that
-// bounds the row's largest magnitude (the two threads holding a row exchange
-// their halves' bounds through a 64-arrival mbarrier); delta4 = w5 * silu'(z4)
+// bounds the row's largest magnitude (the four threads holding a row exchange
+// their bounds through a 128-arrival mbarrier); delta4 = w5 * silu'(z4)
 // uses the fixed bound 1.1 max |w5|.  The accumulator of the next layer is
 // rescaled by (row scale) x (column scale) before bias and activation.
 // Every wait is bounded (2 s on the global timer): on timeout the kernel sets
@@ -44,8 +44,10 @@ namespace spider {
 namespace {
 
 constexpr int kRows = 128;          // pairs per tile = MMA M = TMEM lanes
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kGroups = kEpiWarps / 4;     // column groups per TMEM lane quarter
 constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kCc = 16;                     // columns per epilogue chunk
 constexpr int kTcThreads = kEpiThreads + 64;
 constexpr int kStages = 2;
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -58,7 +60,7 @@ struct Cfg {
   static constexpr int kImage = H * H * EB;         // bytes of one weight image
   static constexpr int kA = kRows * H * EB;         // activations, SW128 K-major
   static constexpr int kD3 = kRows * H * 2;         // silu'(z3), BF16
-  static constexpr int kHalf = H / 2;               // columns per epilogue thread
+  static constexpr int kCols = H / kGroups;         // columns per epilogue thread
   static constexpr int kTmemCols = 2 * H;
   static constexpr int kChunksPerTile = 6 * KB;
   // shared-memory carve-up (offsets from a 1024-aligned base)
@@ -67,9 +69,9 @@ struct Cfg {
   static constexpr int oD3 = oB + kStages * kChunk;
   static constexpr int oPar = oD3 + kD3;                  // W1 (6H), b1, b2, b3, b4, w5 (5H) floats
   static constexpr int oSc = oPar + 11 * H * 4;           // FP8: column scales of the 6 images (6H floats)
-  static constexpr int oXch = oSc + (F8 ? 6 * H * 4 : 0); // FP8: row-bound exchange [2][2][kRows] floats
-  static constexpr int oRed = oXch + (F8 ? 4 * kRows * 4 : 0);   // [4][2][kRows] floats
-  static constexpr int oBar = oRed + 4 * 2 * kRows * 4;   // mbarriers
+  static constexpr int oXch = oSc + (F8 ? 6 * H * 4 : 0); // FP8: row-bound exchange [2][kGroups][kRows] floats
+  static constexpr int oRed = oXch + (F8 ? 2 * kGroups * kRows * 4 : 0);   // [4][kGroups][kRows] floats
+  static constexpr int oBar = oRed + 4 * kGroups * kRows * 4;   // mbarriers
   static constexpr int oMisc = oBar + 16 * 8;             // tmem base, abort flag
   static constexpr int kSmem = oMisc + 16 + 1024;         // + alignment slack
 };
@@ -195,6 +197,25 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16f(uint32_t taddr, float (&v)[16]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -237,15 +258,21 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-// FP8: largest magnitude bound of a row over both column halves (bounded wait)
-__device__ __forceinline__ bool pair_max(float& m, float* xch, uint64_t* xbar, uint32_t& xph, int half, int r,
-                                         volatile int* abort_flag, int32_t* gerr) {
+// FP8: largest magnitude bound of a row over its column groups (bounded wait);
+// every thread of the row takes the maximum in the same order
+__device__ __forceinline__ bool group_max(float& m, float* xch, uint64_t* xbar, uint32_t& xph, int cg, int r,
+                                          volatile int* abort_flag, int32_t* gerr) {
   const int slot = (int)(xph & 1);
-  xch[(slot * 2 + half) * kRows + r] = m;
+  xch[(slot * kGroups + cg) * kRows + r] = m;
   mbar_arrive(xbar);
   const bool got = mbar_wait(xbar, xph & 1, abort_flag, gerr);
   xph ^= 1;
-  if (got) m = fmaxf(m, xch[(slot * 2 + (half ^ 1)) * kRows + r]);
+  if (got) {
+    float a = xch[(slot * kGroups) * kRows + r];
+#pragma unroll
+    for (int q = 1; q < kGroups; ++q) a = fmaxf(a, xch[(slot * kGroups + q) * kRows + r]);
+    m = a;
+  }
   return got;
 }
 
@@ -289,7 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(a_ready, kEpiThreads);
     mbar_init(drain, 1);
     mbar_init(red_ready, kEpiThreads);
-    for (int q = 0; q < 4; ++q) mbar_init(&xbar[q], 64);
+    for (int q = 0; q < 4; ++q) mbar_init(&xbar[q], 32 * kGroups);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -379,10 +406,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int g = warp & 3, half = warp >> 2;
+    const int g = warp & 3, cg = warp >> 2;
     const int r = g * 32 + lane;                       // tile row = TMEM lane
     const uint32_t lane_addr = tmem + ((uint32_t)(g * 32) << 16);
-    const int c0 = half * C::kHalf;                    // first column of this thread
+    const int c0 = cg * C::kCols;                      // first column of this thread
     uint32_t acc_phase = 0, red_phase = 0, xph = 0;
     for (int64_t t = 0; t < my_tiles; ++t) {
       const int64_t u0 = (blockIdx.x + t * gridDim.x) * kRows;
@@ -400,73 +427,88 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
       bool ok = true;
-      if constexpr (F8) {
-        float sa;                      // dequantisation scale of this row of the A operand
-        // layer 1 in FP32; h1 -> A (E4M3, row scale), silu'(z1) -> TMEM [H, 3H/2)
-        {
-          float m = 0.2785f;           // silu(z) >= -0.2785
-          for (int cc = 0; cc < C::kHalf; ++cc) {
+      float sa = 1.f;                                  // FP8: dequantisation scale of this A row
+      // ---- layer 1 in FP32: h1 -> A, silu'(z1) -> TMEM [H, 3H/2)
+      {
+        float inv = 1.f;
+        if constexpr (F8) {
+          float m = 0.2785f;                           // silu(z) >= -0.2785
+          for (int cc = 0; cc < C::kCols; ++cc) {
             const int col = c0 + cc;
             float z = pb1[col];
 #pragma unroll
             for (int c = 0; c < 6; ++c) z = fmaf(pW1[col * 6 + c], x[c], z);
             m = fmaxf(m, z);
           }
-          const bool got = pair_max(m, xch, &xbar[g], xph, half, r, abort_flag, gerr);
+          const bool got = group_max(m, xch, &xbar[g], xph, cg, r, abort_flag, gerr);
           if (!__all_sync(0xffffffffu, got)) break;
-          const float inv = 448.f / m;
+          inv = 448.f / m;
           sa = m / 448.f;
-          for (int cc = 0; cc < C::kHalf; cc += 32) {
-            const int col = c0 + cc;
-            uint32_t hq[8], dp[16];
-#pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              float h[4], d[4];
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                float z = pb1[col + i + q];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) z = fmaf(pW1[(col + i + q) * 6 + c], x[c], z);
-                silu_tc(z, h[q], d[q]);
-              }
-              hq[i / 4] = pack_e4m3x4(h[0] * inv, h[1] * inv, h[2] * inv, h[3] * inv);
-              dp[i / 2] = pack_bf16(d[0], d[1]);
-              dp[i / 2 + 1] = pack_bf16(d[2], d[3]);
-            }
-            *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
-            *reinterpret_cast<uint4*>(sA + a_off8(r, col + 16)) = make_uint4(hq[4], hq[5], hq[6], hq[7]);
-            tmem_st16(lane_addr + H + col / 2, dp);
-          }
-          tmem_wait_st();
-          fence_async_smem();
-          tc_before();
-          mbar_arrive(a_ready);
         }
-        for (int layer = 0; layer < 6; ++layer) {
-          const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
-          if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
-          acc_phase ^= 1;
-          tc_after();
-          const float* sw = wsc + layer * H;
-          // bound of the row for the next A operand (layers 0, 1: silu(z); 3, 4: delta)
-          float inv = 0.f, sa_next = sa;
+        for (int cc = 0; cc < C::kCols; cc += kCc) {
+          const int col = c0 + cc;
+          float h[kCc];
+          uint32_t dp[kCc / 2];
+#pragma unroll
+          for (int i = 0; i < kCc; i += 2) {
+            float z0 = pb1[col + i], z1 = pb1[col + i + 1];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              z0 = fmaf(pW1[(col + i) * 6 + c], x[c], z0);
+              z1 = fmaf(pW1[(col + i + 1) * 6 + c], x[c], z1);
+            }
+            float d0, d1;
+            silu_tc(z0, h[i], d0);
+            silu_tc(z1, h[i + 1], d1);
+            dp[i / 2] = pack_bf16(d0, d1);
+          }
+          if constexpr (F8) {
+            uint32_t hq[4];
+#pragma unroll
+            for (int i = 0; i < kCc; i += 4)
+              hq[i / 4] = pack_e4m3x4(h[i] * inv, h[i + 1] * inv, h[i + 2] * inv, h[i + 3] * inv);
+            *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
+          } else {
+            uint32_t hp[8];
+#pragma unroll
+            for (int i = 0; i < kCc; i += 2) hp[i / 2] = pack_bf16(h[i], h[i + 1]);
+            *reinterpret_cast<uint4*>(sA + a_off(r, col)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+            *reinterpret_cast<uint4*>(sA + a_off(r, col + 8)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+          }
+          tmem_st8(lane_addr + H + col / 2, dp);
+        }
+        tmem_wait_st();
+        fence_async_smem();
+        tc_before();
+        mbar_arrive(a_ready);
+      }
+      // ---- hidden layers (forward) and the reverse sweep
+      for (int layer = 0; layer < 6; ++layer) {
+        const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        acc_phase ^= 1;
+        tc_after();
+        const float* sw = wsc + layer * H;             // FP8 column scales of this image
+        float inv = 1.f, sa_next = sa;
+        if constexpr (F8) {
           if (layer == 0 || layer == 1 || layer == 3 || layer == 4) {
+            // bound of the row for the next A operand (silu(z) forward, delta backward)
             const float* bias = pb + layer * H;
             float m = layer <= 1 ? 0.2785f : 1e-30f;
-            for (int cc = 0; cc < C::kHalf; cc += 32) {
+            for (int cc = 0; cc < C::kCols; cc += kCc) {
               const int col = c0 + cc;
-              float v[32];
-              tmem_ld32(lane_addr + col, v);
+              float v[kCc];
+              tmem_ld16f(lane_addr + col, v);
               tmem_wait_ld();
               if (layer <= 1) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) m = fmaxf(m, fmaf(v[i], sa * sw[col + i], bias[col + i]));
+                for (int i = 0; i < kCc; ++i) m = fmaxf(m, fmaf(v[i], sa * sw[col + i], bias[col + i]));
               } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) m = fmaxf(m, 1.1f * fabsf(v[i] * (sa * sw[col + i])));
+                for (int i = 0; i < kCc; ++i) m = fmaxf(m, 1.1f * fabsf(v[i] * (sa * sw[col + i])));
               }
             }
-            const bool got2 = pair_max(m, xch, &xbar[g], xph, half, r, abort_flag, gerr);
+            const bool got2 = group_max(m, xch, &xbar[g], xph, cg, r, abort_flag, gerr);
             if (!__all_sync(0xffffffffu, got2)) { ok = false; break; }
             inv = 448.f / m;
             sa_next = m / 448.f;
@@ -474,202 +516,112 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             inv = 1.f / s4;
             sa_next = s4;
           }
-          for (int cc = 0; cc < C::kHalf; cc += 32) {
-            const int col = c0 + cc;
-            float v[32];
-            tmem_ld32(lane_addr + col, v);
-            tmem_wait_ld();
-            uint32_t hq[8], dp[16];
-            if (layer < 3) {
-              const float* bias = pb + layer * H;
-#pragma unroll
-              for (int i = 0; i < 32; i += 4) {
-                float h[4], d[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) silu_tc(fmaf(v[i + q], sa * sw[col + i + q], bias[col + i + q]), h[q], d[q]);
-                if (layer == 2) {
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) tpart = fmaf(pw5[col + i + q], h[q], tpart);
-                  hq[i / 4] = pack_e4m3x4(pw5[col + i] * d[0] * inv, pw5[col + i + 1] * d[1] * inv,
-                                          pw5[col + i + 2] * d[2] * inv, pw5[col + i + 3] * d[3] * inv);
-                } else {
-                  hq[i / 4] = pack_e4m3x4(h[0] * inv, h[1] * inv, h[2] * inv, h[3] * inv);
-                  dp[i / 2] = pack_bf16(d[0], d[1]);
-                  dp[i / 2 + 1] = pack_bf16(d[2], d[3]);
-                }
-              }
-              if (layer == 0) {
-                tmem_st16(lane_addr + H + C::kHalf + col / 2, dp);                 // silu'(z2)
-              } else if (layer == 1) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)                                         // silu'(z3)
-                  *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8 * q)) =
-                      make_uint4(dp[4 * q], dp[4 * q + 1], dp[4 * q + 2], dp[4 * q + 3]);
-              }
-            } else {
-              uint32_t dd[16];
-              if (layer == 3) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const uint4 w4 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8 * q));
-                  dd[4 * q] = w4.x; dd[4 * q + 1] = w4.y; dd[4 * q + 2] = w4.z; dd[4 * q + 3] = w4.w;
-                }
-              } else {
-                tmem_ld16(lane_addr + H + (layer == 4 ? C::kHalf : 0) + col / 2, dd);
-                tmem_wait_ld();
-              }
-              float e[32];
-#pragma unroll
-              for (int i = 0; i < 32; i += 2) {
-                e[i] = v[i] * (sa * sw[col + i]) * bf16_lo(dd[i / 2]);
-                e[i + 1] = v[i + 1] * (sa * sw[col + i + 1]) * bf16_hi(dd[i / 2]);
-              }
-              if (layer == 5) {
-#pragma unroll
-                for (int i = 0; i < 32; ++i)
-#pragma unroll
-                  for (int c = 0; c < 3; ++c) gpart[c] = fmaf(pW1[(col + i) * 6 + c], e[i], gpart[c]);
-              } else {
-#pragma unroll
-                for (int i = 0; i < 32; i += 4)
-                  hq[i / 4] = pack_e4m3x4(e[i] * inv, e[i + 1] * inv, e[i + 2] * inv, e[i + 3] * inv);
-              }
-            }
-            if (layer < 5) {
-              *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
-              *reinterpret_cast<uint4*>(sA + a_off8(r, col + 16)) = make_uint4(hq[4], hq[5], hq[6], hq[7]);
-            }
-          }
-          sa = sa_next;
-          if (layer == 0) tmem_wait_st();
-          if (layer < 5) {
-            fence_async_smem();
-            tc_before();
-            mbar_arrive(a_ready);
-          }
         }
-      } else {
-        // layer 1 in FP32: h1 -> A (BF16), silu'(z1) -> TMEM [H, 3H/2)
-        for (int cc = 0; cc < C::kHalf; cc += 32) {
+        for (int cc = 0; cc < C::kCols; cc += kCc) {
           const int col = c0 + cc;
-          uint32_t hp[16], dp[16];
-  #pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            float z0 = pb1[col + i], z1 = pb1[col + i + 1];
-  #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-              z0 = fmaf(pW1[(col + i) * 6 + c], x[c], z0);
-              z1 = fmaf(pW1[(col + i + 1) * 6 + c], x[c], z1);
-            }
-            float h0, d0, h1, d1;
-            silu_tc(z0, h0, d0);
-            silu_tc(z1, h1, d1);
-            hp[i / 2] = pack_bf16(h0, h1);
-            dp[i / 2] = pack_bf16(d0, d1);
+          float v[kCc];
+          tmem_ld16f(lane_addr + col, v);
+          tmem_wait_ld();
+          if constexpr (F8) {
+#pragma unroll
+            for (int i = 0; i < kCc; ++i) v[i] *= sa * sw[col + i];
           }
-  #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
-                make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
-          tmem_st16(lane_addr + H + col / 2, dp);
-        }
-        tmem_wait_st();
-        fence_async_smem();
-        tc_before();
-        mbar_arrive(a_ready);
-
-        for (int layer = 0; layer < 6; ++layer) {
-          const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
-          if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
-          acc_phase ^= 1;
-          tc_after();
-          for (int cc = 0; cc < C::kHalf; cc += 32) {
-            const int col = c0 + cc;
-            float v[32];
-            tmem_ld32(lane_addr + col, v);
-            tmem_wait_ld();
-            uint32_t hp[16], dp[16];
-            if (layer < 3) {
-              // forward layers 2..4
-              const float* bias = pb + layer * H;
-  #pragma unroll
-              for (int i = 0; i < 32; i += 2) {
-                float h0, d0, h1, d1;
-                silu_tc(v[i] + bias[col + i], h0, d0);
-                silu_tc(v[i + 1] + bias[col + i + 1], h1, d1);
-                if (layer == 2) {
-                  const float w0 = pw5[col + i], w1 = pw5[col + i + 1];
-                  tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
-                  hp[i / 2] = pack_bf16(w0 * d0, w1 * d1);     // delta4
-                } else {
-                  hp[i / 2] = pack_bf16(h0, h1);
-                  dp[i / 2] = pack_bf16(d0, d1);
-                }
-              }
-              if (layer == 0) {
-                tmem_st16(lane_addr + H + C::kHalf + col / 2, dp);                 // silu'(z2)
-              } else if (layer == 1) {
-  #pragma unroll
-                for (int q = 0; q < 4; ++q)                                         // silu'(z3)
-                  *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8 * q)) =
-                      make_uint4(dp[4 * q], dp[4 * q + 1], dp[4 * q + 2], dp[4 * q + 3]);
-              }
-            } else {
-              // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
-              uint32_t dd[16];
-              if (layer == 3) {
-  #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const uint4 w4 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8 * q));
-                  dd[4 * q] = w4.x; dd[4 * q + 1] = w4.y; dd[4 * q + 2] = w4.z; dd[4 * q + 3] = w4.w;
-                }
+          float o[kCc];                                // next A operand values (unscaled)
+          if (layer < 3) {
+            // forward layers 2..4
+            const float* bias = pb + layer * H;
+            uint32_t dp[kCc / 2];
+#pragma unroll
+            for (int i = 0; i < kCc; i += 2) {
+              float h0, d0, h1, d1;
+              silu_tc(v[i] + bias[col + i], h0, d0);
+              silu_tc(v[i + 1] + bias[col + i + 1], h1, d1);
+              if (layer == 2) {
+                const float w0 = pw5[col + i], w1 = pw5[col + i + 1];
+                tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
+                o[i] = w0 * d0;                        // delta4
+                o[i + 1] = w1 * d1;
               } else {
-                tmem_ld16(lane_addr + H + (layer == 4 ? C::kHalf : 0) + col / 2, dd);
-                tmem_wait_ld();
-              }
-  #pragma unroll
-              for (int i = 0; i < 32; i += 2) {
-                const float e0 = v[i] * bf16_lo(dd[i / 2]);
-                const float e1 = v[i + 1] * bf16_hi(dd[i / 2]);
-                if (layer == 5) {
-  #pragma unroll
-                  for (int c = 0; c < 3; ++c)
-                    gpart[c] = fmaf(pW1[(col + i) * 6 + c], e0, fmaf(pW1[(col + i + 1) * 6 + c], e1, gpart[c]));
-                } else {
-                  hp[i / 2] = pack_bf16(e0, e1);
-                }
+                o[i] = h0;
+                o[i + 1] = h1;
+                dp[i / 2] = pack_bf16(d0, d1);
               }
             }
-            if (layer < 5) {
-  #pragma unroll
-              for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(sA + a_off(r, col + 8 * q)) =
-                    make_uint4(hp[4 * q], hp[4 * q + 1], hp[4 * q + 2], hp[4 * q + 3]);
+            if (layer == 0) {
+              tmem_st8(lane_addr + H + H / 2 + col / 2, dp);                          // silu'(z2)
+            } else if (layer == 1) {
+              *reinterpret_cast<uint4*>(sD3 + d3_off(r, col)) = make_uint4(dp[0], dp[1], dp[2], dp[3]);
+              *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8)) = make_uint4(dp[4], dp[5], dp[6], dp[7]);
+            }
+          } else {
+            // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
+            uint32_t dd[kCc / 2];
+            if (layer == 3) {
+              const uint4 w0 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col));
+              const uint4 w1 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8));
+              dd[0] = w0.x; dd[1] = w0.y; dd[2] = w0.z; dd[3] = w0.w;
+              dd[4] = w1.x; dd[5] = w1.y; dd[6] = w1.z; dd[7] = w1.w;
+            } else {
+              tmem_ld8(lane_addr + H + (layer == 4 ? H / 2 : 0) + col / 2, dd);
+              tmem_wait_ld();
+            }
+#pragma unroll
+            for (int i = 0; i < kCc; i += 2) {
+              o[i] = v[i] * bf16_lo(dd[i / 2]);
+              o[i + 1] = v[i + 1] * bf16_hi(dd[i / 2]);
+            }
+            if (layer == 5) {
+#pragma unroll
+              for (int i = 0; i < kCc; ++i)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gpart[c] = fmaf(pW1[(col + i) * 6 + c], o[i], gpart[c]);
             }
           }
-          if (layer == 0) tmem_wait_st();
           if (layer < 5) {
-            fence_async_smem();
-            tc_before();
-            mbar_arrive(a_ready);
+            if constexpr (F8) {
+              uint32_t hq[4];
+#pragma unroll
+              for (int i = 0; i < kCc; i += 4)
+                hq[i / 4] = pack_e4m3x4(o[i] * inv, o[i + 1] * inv, o[i + 2] * inv, o[i + 3] * inv);
+              *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
+            } else {
+              uint32_t hp[8];
+#pragma unroll
+              for (int i = 0; i < kCc; i += 2) hp[i / 2] = pack_bf16(o[i], o[i + 1]);
+              *reinterpret_cast<uint4*>(sA + a_off(r, col)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+              *reinterpret_cast<uint4*>(sA + a_off(r, col + 8)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+            }
           }
+        }
+        sa = sa_next;
+        if (layer == 0) tmem_wait_st();
+        if (layer < 5) {
+          fence_async_smem();
+          tc_before();
+          mbar_arrive(a_ready);
         }
       }
       if (!ok) break;
       tc_before();
-      // combine the two column halves of each row and write T, dT/dx
-      red[(0 * 2 + half) * kRows + r] = tpart;
+      // combine the column groups of each row (fixed order) and write T, dT/dx
+      red[(0 * kGroups + cg) * kRows + r] = tpart;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) red[((1 + c) * 2 + half) * kRows + r] = gpart[c];
+      for (int c = 0; c < 3; ++c) red[((1 + c) * kGroups + cg) * kRows + r] = gpart[c];
       mbar_arrive(red_ready);
       const bool got = mbar_wait(red_ready, red_phase, abort_flag, gerr);
       red_phase ^= 1;
       if (!__all_sync(0xffffffffu, got)) break;
-      if (half == 0 && valid) {
-        const float dtau = red[0 * kRows + r] + red[1 * kRows + r];
+      if (cg == 0 && valid) {
+        float dtau = red[0 * kGroups * kRows + r];
         float gt[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gt[c] = red[((1 + c) * 2) * kRows + r] + red[((1 + c) * 2 + 1) * kRows + r];
+        for (int c = 0; c < 3; ++c) gt[c] = red[((1 + c) * kGroups) * kRows + r];
+#pragma unroll
+        for (int q = 1; q < kGroups; ++q) {
+          dtau += red[(0 * kGroups + q) * kRows + r];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) gt[c] += red[((1 + c) * kGroups + q) * kRows + r];
+        }
         PairGeo pg;
         load_pair(src, u, pg);
         df32 d[3];

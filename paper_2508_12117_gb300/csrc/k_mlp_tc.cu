@@ -49,7 +49,7 @@ constexpr int kGroups = kEpiWarps / 4;     // column groups per TMEM lane quarte
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kCc = 16;                     // columns per epilogue chunk
 constexpr int kTcThreads = kEpiThreads + 64;
-constexpr int kStages = 2;
+constexpr int kStages = 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 template <int H, bool F8>
@@ -59,15 +59,14 @@ struct Cfg {
   static constexpr int kChunk = H * 128;            // bytes of one weight K-block (H rows x 128 B)
   static constexpr int kImage = H * H * EB;         // bytes of one weight image
   static constexpr int kA = kRows * H * EB;         // activations, SW128 K-major
-  static constexpr int kD3 = kRows * H * 2;         // silu'(z3), BF16
+  static constexpr int kD3 = kRows * H * 2;         // silu'(z3), BF16, per-CTA slot in global memory
   static constexpr int kCols = H / kGroups;         // columns per epilogue thread
   static constexpr int kTmemCols = 2 * H;
   static constexpr int kChunksPerTile = 6 * KB;
   // shared-memory carve-up (offsets from a 1024-aligned base)
   static constexpr int oA = 0;
   static constexpr int oB = oA + kA;
-  static constexpr int oD3 = oB + kStages * kChunk;
-  static constexpr int oPar = oD3 + kD3;                  // W1 (6H), b1, b2, b3, b4, w5 (5H) floats
+  static constexpr int oPar = oB + kStages * kChunk;      // W1 (6H), b1, b2, b3, b4, w5 (5H) floats
   static constexpr int oSc = oPar + 11 * H * 4;           // FP8: column scales of the 6 images (6H floats)
   static constexpr int oXch = oSc + (F8 ? 6 * H * 4 : 0); // FP8: row-bound exchange [2][kGroups][kRows] floats
   static constexpr int oRed = oXch + (F8 ? 2 * kGroups * kRows * 4 : 0);   // [4][kGroups][kRows] floats
@@ -281,13 +280,16 @@ __device__ __forceinline__ uint32_t d3_off(int r, int c) { return (uint32_t)(((c
 
 template <int H, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tt_mlp_tc(NetView net, PairSource src, TTOut out, const uint8_t* __restrict__ wimg, int32_t* gerr) {
+    k_tt_mlp_tc(NetView net, PairSource src, TTOut out, const uint8_t* __restrict__ wimg, int32_t* gerr,
+                uint8_t* __restrict__ stash) {
   using C = Cfg<H, F8>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm + C::oA;
   uint8_t* sB = sm + C::oB;
-  uint8_t* sD3 = sm + C::oD3;
+  // silu'(z3) of the current tile: this CTA's slot in global memory (each thread
+  // reads back only what it wrote)
+  uint8_t* sD3 = stash + (size_t)blockIdx.x * C::kD3;
   float* pW1 = reinterpret_cast<float*>(sm + C::oPar);
   float* pb1 = pW1 + 6 * H;
   float* pb = pb1 + H;       // b2, b3, b4
@@ -296,22 +298,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float* wsc = reinterpret_cast<float*>(sm + C::oSc);     // FP8 column scales [6][H]
   float* xch = reinterpret_cast<float*>(sm + C::oXch);    // FP8 row-bound exchange
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::oBar);
-  uint64_t* full = bars;           // [2] weight stage loaded
-  uint64_t* empty = bars + 2;      // [2] weight stage consumed
-  uint64_t* acc_ready = bars + 4;  // accumulator complete
-  uint64_t* a_ready = bars + 5;    // epilogue done with TMEM reads + A written
-  uint64_t* drain = bars + 6;      // MMA drain on abort
-  uint64_t* red_ready = bars + 7;  // both column halves of every row reduced
-  uint64_t* xbar = bars + 8;       // [4] FP8 row-bound exchange of warps g and g + 4
+  uint64_t* full = bars;                     // [kStages] weight stage loaded
+  uint64_t* empty = bars + kStages;          // [kStages] weight stage consumed
+  uint64_t* acc_ready = bars + 2 * kStages;  // accumulator complete
+  uint64_t* a_ready = acc_ready + 1;         // epilogue done with TMEM reads + A written
+  uint64_t* drain = acc_ready + 2;           // MMA drain on abort
+  uint64_t* red_ready = acc_ready + 3;       // every column group of every row reduced
+  uint64_t* xbar = acc_ready + 4;            // [4] FP8 row-bound exchange within a lane quarter
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + C::oMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + C::oMisc + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], 1);
-    mbar_init(&empty[1], 1);
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
     mbar_init(acc_ready, 1);
     mbar_init(a_ready, kEpiThreads);
     mbar_init(drain, 1);
@@ -350,8 +352,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int64_t total = my_tiles * C::kChunksPerTile;
       int64_t n = 0;
       for (; n < total; ++n) {
-        const int s = (int)(n & 1);
-        const int64_t use = n >> 1;
+        const int s = (int)(n % kStages);
+        const int64_t use = n / kStages;
         if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), abort_flag, gerr)) break;
         const int c = (int)(n % C::kChunksPerTile);
         const uint8_t* g = wimg + (size_t)(c / C::KB) * C::kImage + (size_t)(c % C::KB) * C::kChunk;
@@ -360,9 +362,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       // copies still in flight must land before the CTA's shared memory goes away
       for (int64_t m = (n > kStages ? n - kStages : 0); m < n; ++m) {
-        const int s = (int)(m & 1);
+        const int s = (int)(m % kStages);
         const uint64_t t0 = gtime();
-        while (!mbar_test(&full[s], (uint32_t)((m >> 1) & 1)))
+        while (!mbar_test(&full[s], (uint32_t)((m / kStages) & 1)))
           if (gtime() - t0 > kWaitNs) break;
       }
     }
@@ -381,8 +383,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           a_phase ^= 1;
           tc_after();
           for (int kb = 0; kb < C::KB; ++kb, ++n) {
-            const int s = (int)(n & 1);
-            if (!mbar_wait(&full[s], (uint32_t)((n >> 1) & 1), abort_flag, gerr)) { ok = false; break; }
+            const int s = (int)(n % kStages);
+            if (!mbar_wait(&full[s], (uint32_t)((n / kStages) & 1), abort_flag, gerr)) { ok = false; break; }
             tc_after();
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -646,11 +648,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 template <int H, bool F8>
-cudaError_t launch_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, cudaStream_t st) {
+cudaError_t launch_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, float* scratch,
+                      cudaStream_t st) {
   using C = Cfg<H, F8>;
   cudaError_t e = cudaFuncSetAttribute(k_tt_mlp_tc<H, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   if (e != cudaSuccess) return e;
-  k_tt_mlp_tc<H, F8><<<num_sms, kTcThreads, C::kSmem, st>>>(net, src, out, (const uint8_t*)net.tc, net.err);
+  k_tt_mlp_tc<H, F8><<<num_sms, kTcThreads, C::kSmem, st>>>(net, src, out, (const uint8_t*)net.tc, net.err,
+                                                             reinterpret_cast<uint8_t*>(scratch));
   return cudaGetLastError();
 }
 
@@ -732,21 +736,23 @@ cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, 
   return cudaSuccess;
 }
 
-cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, cudaStream_t st) {
-  if (!net.tc || !net.err) return cudaErrorNotSupported;
+// scratch: num_sms x 128 x H BF16 (the silu'(z3) slots), see tt_scratch_floats
+cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, float* scratch,
+                          cudaStream_t st) {
+  if (!net.tc || !net.err || !scratch) return cudaErrorNotSupported;
   if (net.precision == SPIDER_FP8) {
     if (!net.tc_scale) return cudaErrorNotSupported;
     switch (net.H) {
-      case 128: return launch_tc<128, true>(net, src, out, num_sms, st);
-      case 256: return launch_tc<256, true>(net, src, out, num_sms, st);
+      case 128: return launch_tc<128, true>(net, src, out, num_sms, scratch, st);
+      case 256: return launch_tc<256, true>(net, src, out, num_sms, scratch, st);
       default: return cudaErrorNotSupported;
     }
   }
   if (net.precision != SPIDER_BF16) return cudaErrorNotSupported;
   switch (net.H) {
-    case 64: return launch_tc<64, false>(net, src, out, num_sms, st);
-    case 128: return launch_tc<128, false>(net, src, out, num_sms, st);
-    case 256: return launch_tc<256, false>(net, src, out, num_sms, st);
+    case 64: return launch_tc<64, false>(net, src, out, num_sms, scratch, st);
+    case 128: return launch_tc<128, false>(net, src, out, num_sms, scratch, st);
+    case 256: return launch_tc<256, false>(net, src, out, num_sms, scratch, st);
     default: return cudaErrorNotSupported;
   }
 }

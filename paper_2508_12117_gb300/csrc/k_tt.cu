@@ -264,7 +264,9 @@ int mlp_fp32_grid(int num_sms) { return 2 * num_sms; }
 
 size_t tt_scratch_floats(const NetView& net, int num_sms) {
   if (net.kind != SPIDER_TT_MLP) return 0;
-  return (size_t)mlp_fp32_grid(num_sms) * 3 * net.H * kTP;
+  const size_t fp32 = (size_t)mlp_fp32_grid(num_sms) * 3 * net.H * kTP;
+  const size_t tc = (size_t)num_sms * 128 * net.H / 2;     // 128 x H BF16 per SM
+  return fp32 > tc ? fp32 : tc;
 }
 
 bool tt_supported_width(int H) { return H == 32 || H == 64 || H == 128 || H == 256; }
@@ -280,7 +282,7 @@ cudaError_t launch_tt(const NetView& net, const PairSource& src, TTOut out, int 
     return cudaGetLastError();
   }
   if (net.precision != SPIDER_FP32) {
-    cudaError_t e = launch_mlp_tc(net, src, out, num_sms, st);
+    cudaError_t e = launch_mlp_tc(net, src, out, num_sms, scratch, st);
     if (e != cudaErrorNotSupported) return e;
     return cudaErrorNotSupported;
   }

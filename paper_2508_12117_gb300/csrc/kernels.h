@@ -16,7 +16,7 @@ size_t tt_scratch_floats(const NetView& net, int num_sms);
 cudaError_t launch_tt(const NetView& net, const PairSource& src, TTOut out, int num_sms, float* scratch,
                       cudaStream_t st, int ctas_per_sm);
 cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms,
-                          cudaStream_t st);
+                          float* scratch, cudaStream_t st);
 bool mlp_tc_supported(int H, int precision);
 // builds the tensor-core operand images of the hidden layers on the device
 cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, int H, int precision,

@@ -13,6 +13,8 @@
 //              lane) and columns [ (w / 4) H/4, (w / 4 + 1) H/4 ), 16 at a time;
 //   warp 16    producer: 1-D bulk async copies (cp.async.bulk) of pre-swizzled
 //              weight K-blocks (H rows x 64 BF16) into a two-stage ring;
+//   warp 18    geometry: loads the (event, station) geometry of the next tile
+//              into a shared-memory double buffer while the current tile runs;
 //   warp 17    MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = H,
 //              K = 16, A = activations (SW128 K-major, shared memory),
 //              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
@@ -48,8 +50,8 @@ constexpr int kEpiWarps = 16;
 constexpr int kGroups = kEpiWarps / 4;     // column groups per TMEM lane quarter
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kCc = 16;                     // columns per epilogue chunk
-constexpr int kTcThreads = kEpiThreads + 64;
-constexpr int kStages = 4;
+constexpr int kTcThreads = kEpiThreads + 96;   // + producer, MMA issuer, geometry warps
+constexpr int kStages = 3;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 template <int H, bool F8>
@@ -70,7 +72,8 @@ struct Cfg {
   static constexpr int oSc = oPar + 11 * H * 4;           // FP8: column scales of the 6 images (6H floats)
   static constexpr int oXch = oSc + (F8 ? 6 * H * 4 : 0); // FP8: row-bound exchange [2][kGroups][kRows] floats
   static constexpr int oRed = oXch + (F8 ? 2 * kGroups * kRows * 4 : 0);   // [4][kGroups][kRows] floats
-  static constexpr int oBar = oRed + 4 * kGroups * kRows * 4;   // mbarriers
+  static constexpr int oGeo = oRed + 4 * kGroups * kRows * 4;   // pair geometry [2][15][kRows] floats
+  static constexpr int oBar = oGeo + 2 * 15 * kRows * 4;         // mbarriers
   static constexpr int oMisc = oBar + 16 * 8;             // tmem base, abort flag
   static constexpr int kSmem = oMisc + 16 + 1024;         // + alignment slack
 };
@@ -305,6 +308,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* drain = acc_ready + 2;           // MMA drain on abort
   uint64_t* red_ready = acc_ready + 3;       // every column group of every row reduced
   uint64_t* xbar = acc_ready + 4;            // [4] FP8 row-bound exchange within a lane quarter
+  uint64_t* geo_full = acc_ready + 8;        // [2] geometry buffer filled
+  uint64_t* geo_empty = acc_ready + 10;      // [2] geometry buffer released by the epilogue
+  float* geo = reinterpret_cast<float*>(sm + C::oGeo);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + C::oMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + C::oMisc + 4);
 
@@ -319,6 +325,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(drain, 1);
     mbar_init(red_ready, kEpiThreads);
     for (int q = 0; q < 4; ++q) mbar_init(&xbar[q], 32 * kGroups);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&geo_full[q], 32);
+      mbar_init(&geo_empty[q], kEpiThreads);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -367,6 +377,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         while (!mbar_test(&full[s], (uint32_t)((m / kStages) & 1)))
           if (gtime() - t0 > kWaitNs) break;
       }
+    }
+  } else if (warp == kEpiWarps + 2) {
+    // ------------------------------------------------------------ geometry prefetch
+    for (int64_t t = 0; t < my_tiles; ++t) {
+      const int b = (int)(t & 1);
+      if (t >= 2) {
+        const bool got = mbar_wait(&geo_empty[b], (uint32_t)(((t - 2) >> 1) & 1), abort_flag, gerr);
+        if (!__all_sync(0xffffffffu, got)) break;
+      }
+      const int64_t u0 = (blockIdx.x + t * gridDim.x) * kRows;
+      float* gb = geo + b * 15 * kRows;
+      for (int r = lane; r < kRows; r += 32) {
+        PairGeo pg;
+        load_pair(src, u0 + r < P ? u0 + r : u0, pg);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          gb[(0 + c) * kRows + r] = pg.shi[c];
+          gb[(3 + c) * kRows + r] = pg.slo[c];
+          gb[(6 + c) * kRows + r] = pg.soff[c];
+          gb[(9 + c) * kRows + r] = pg.rhi[c];
+          gb[(12 + c) * kRows + r] = pg.rlo[c];
+        }
+      }
+      mbar_arrive(&geo_full[b]);
     }
   } else if (warp == kEpiWarps + 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -417,15 +451,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int64_t u0 = (blockIdx.x + t * gridDim.x) * kRows;
       const int64_t u = u0 + r;
       const bool valid = u < P;
-      float x[6];
+      const int gbuf = (int)(t & 1);
+      const float* gb = geo + gbuf * 15 * kRows;
       {
-        PairGeo pg;
-        load_pair(src, valid ? u : u0, pg);
+        const bool got = mbar_wait(&geo_full[gbuf], (uint32_t)((t >> 1) & 1), abort_flag, gerr);
+        if (!__all_sync(0xffffffffu, got)) break;
+      }
+      float x[6];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          x[c] = pg.shi[c] + (pg.slo[c] + pg.soff[c]);
-          x[3 + c] = pg.rhi[c] + pg.rlo[c];
-        }
+      for (int c = 0; c < 3; ++c) {
+        x[c] = gb[c * kRows + r] + (gb[(3 + c) * kRows + r] + gb[(6 + c) * kRows + r]);
+        x[3 + c] = gb[(9 + c) * kRows + r] + gb[(12 + c) * kRows + r];
       }
       float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
       bool ok = true;
@@ -625,7 +661,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int c = 0; c < 3; ++c) gt[c] += red[((1 + c) * kGroups + q) * kRows + r];
         }
         PairGeo pg;
-        load_pair(src, u, pg);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pg.shi[c] = gb[c * kRows + r];
+          pg.slo[c] = gb[(3 + c) * kRows + r];
+          pg.soff[c] = gb[(6 + c) * kRows + r];
+          pg.rhi[c] = gb[(9 + c) * kRows + r];
+          pg.rlo[c] = gb[(12 + c) * kRows + r];
+        }
         df32 d[3];
         const df32 rr = geometry(pg, d);
         const df32 T = df_add_f(df_mul_f(rr, net.b5), rr.hi * dtau);
@@ -637,6 +680,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                  f * d[2].hi + rr.hi * gt[2], 0.f);
         }
       }
+      mbar_arrive(&geo_empty[gbuf]);       // this tile's geometry buffer may be refilled
     }
   }
   tc_before();

@@ -529,6 +529,7 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   AL(lidx, PP);
   AL(big, PP);
   AL(chist, 512);
+  AL(cc_lroot, Q);
   AL(corder, PP);
   AL(centries, PP);
   AL(ctier, PP);

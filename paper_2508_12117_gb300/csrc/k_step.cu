@@ -441,7 +441,53 @@ __device__ __forceinline__ int32_t cc_root(const int32_t* lab, int32_t u) {
   return r;
 }
 
-__global__ void __launch_bounds__(512) k_cc(StepView v) {
+// Components inside each selected block first (its observations link its local
+// nodes): min-label union-find in shared memory, one CTA per block.  Each local
+// node then records its block-local root; the grid-wide rounds below only
+// have to glue these stars together through pairs shared by several blocks.
+__device__ __forceinline__ int lroot_find(const int* par, int x) {
+  const volatile int* vp = par;
+  for (int k = 0; k < 1 << 16; ++k) {
+    const int p = vp[x];
+    if (p == x) return x;
+    x = p;
+  }
+  return x;
+}
+
+__global__ void k_cc_local(StepView v) {
+  extern __shared__ int par[];
+  __shared__ int changed;
+  const int s = blockIdx.x;
+  const int32_t b = v.sel[s];
+  const int32_t q0 = v.blk_node_off[b];
+  const int L = v.blk_node_off[b + 1] - q0;
+  const int64_t e0 = v.blk_e0[b];
+  const int ne = v.blk_e0[b + 1] - v.blk_e0[b];
+  for (int l = threadIdx.x; l < L; l += blockDim.x) par[l] = l;
+  __syncthreads();
+  for (int round = 0; round < 64; ++round) {
+    if (threadIdx.x == 0) changed = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const uint32_t lij = v.obs_l[e0 + e];
+      int a = lroot_find(par, (int)(lij & 0xFFFF)), c = lroot_find(par, (int)(lij >> 16));
+      if (a == c) continue;
+      const int lo = a < c ? a : c, hi = a < c ? c : a;
+      if (atomicMin(&par[hi], lo) > lo) mine = 1;
+    }
+    if (mine) changed = 1;
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) par[l] = lroot_find(par, l);
+    __syncthreads();
+    if (!changed) break;
+    if (round == 63 && threadIdx.x == 0) set_error(v.counters, SPIDER_E_TIMEOUT);
+  }
+  for (int l = threadIdx.x; l < L; l += blockDim.x) v.cc_lroot[q0 + l] = q0 + par[l];
+}
+
+__global__ void __launch_bounds__(512) k_cc(StepView v, int64_t n_b) {
   __shared__ int any;
   const int32_t P_u = v.counters[kCntPairs];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
@@ -458,14 +504,17 @@ __global__ void __launch_bounds__(512) k_cc(StepView v) {
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     int changed = 0;
-    for (int32_t u = gtid; u < P_u; u += gstride) {
-      int32_t ru = cc_root(v.lab, u);
-      for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
-        const int32_t rc = cc_root(v.lab, v.csr_col[t]);
+    // one link per local node of every selected block: (its pair, its block root's pair)
+    for (int64_t sb = blockIdx.x; sb < n_b; sb += gridDim.x) {
+      const int32_t b = v.sel[sb];
+      const int32_t q0 = v.blk_node_off[b], L = v.blk_node_off[b + 1] - q0;
+      for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        const int32_t q = q0 + l, rq = v.cc_lroot[q];
+        if (rq == q) continue;
+        const int32_t ru = cc_root(v.lab, v.loc2u[q]), rc = cc_root(v.lab, v.loc2u[rq]);
         if (rc == ru) continue;
         const int32_t lo = rc < ru ? rc : ru, hi = rc < ru ? ru : rc;
         if (atomicMin(&v.lab[hi], lo) > lo) changed = 1;
-        ru = cc_root(v.lab, u);
       }
     }
     if (changed) any = 1;
@@ -1822,9 +1871,11 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // connected components
+  k_cc_local<<<(unsigned)n_b, kThreads, (size_t)v.L_max * sizeof(int), st>>>(v);
   {
     StepView vv = v;
-    void* args[] = {&vv};
+    int64_t nb = n_b;
+    void* args[] = {&vv, &nb};
     e = cudaLaunchCooperativeKernel((const void*)k_cc, dim3(grid), dim3(512), args, 0, st);
     if (e != cudaSuccess) return e;
   }

@@ -90,6 +90,25 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(values, world):
+    """Element-wise maximum over the ranks (the slowest replica sets the time)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def replica_rate(world, steps, ms):
+    """Whole-job steps/s: every replica ran `steps` steps within `ms`."""
+    return world * steps / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------- workload
 def build_workload(wid: int):
     from paper_2508_12117_gb300 import synth
@@ -169,11 +188,7 @@ def run_ours(args, rank, world):
         ctx.spider_sgld_step(eps, seed0 + 20_000 + s)
         th_buf, _ = ctx.spider_get_state()
     t_e2e = time.perf_counter() - t_e2e
-    ms = torch.tensor([ms_dev, ms_total, t_e2e * 1e3], dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
-    ms_dev, ms_total, e2e_ms = (float(x) for x in ms)
+    ms_dev, ms_total, e2e_ms = max_over_ranks([ms_dev, ms_total, t_e2e * 1e3], world)
     ctx.close()
     # the other precision forms on the same catalog (graph pass, same seeds)
     forms = {}
@@ -204,7 +219,7 @@ def run_ours(args, rank, world):
                 "kernel": "k_tt_mlp_tc",
                 "peak_source": (f"bf16 sustained x 2 (nominal fp8/bf16 dense ratio), {which}"
                                 if args.precision == "fp8" else f"bf16 sustained, {which}")}
-    steps_s = world * K / (ms_dev * 1e-3)
+    steps_s = replica_rate(world, K, ms_dev)
     state_bytes = cat.M * 16
     line = {
         "metric": METRIC, "value": steps_s, "unit": "steps/s", "n_gpus": world, "steps": K,
@@ -220,7 +235,7 @@ def run_ours(args, rank, world):
                               "residual_whitening": stage[2] / K, "scatter_update": stage[3] / K,
                               "with_host_reads_ms_per_step": ms_total / K},
         "roofline": roof,
-        "e2e": {"value": world * K / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": replica_rate(world, K, e2e_ms), "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": state_bytes,
                 "note": "spider_sgld_step (eps, seed passed by value) + spider_get_state per step"},
         "forms": dict(forms, **({"bf16_over_fp32": steps_s / forms["fp32"]["value"]}
@@ -257,14 +272,11 @@ def time_form(cat, prec_name, eps, seed0, args, stream, world):
         ctx.spider_sgld_step(eps, seed0 + 10_000 + s)
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    ms = max_over_ranks([ev0.elapsed_time(ev1)], world)[0]
     ctx.close()
     K = args.steps
-    return {"value": world * K / (float(ms[0]) * 1e-3), "unit": "steps/s",
-            "ms_per_step": float(ms[0]) / K, "travel_time_mlp_ms": mlp / K}
+    return {"value": replica_rate(world, K, ms), "unit": "steps/s",
+            "ms_per_step": ms / K, "travel_time_mlp_ms": mlp / K}
 
 
 # ---------------------------------------------------------------- batched

@@ -772,34 +772,37 @@ __device__ __forceinline__ int cm_off(int j, int n) { return j * n - (j * (j - 1
 // rows i = j + 1 + lane + 32 s (s < NA) of column j: sum over p < j of L(i, p) L(j, p)
 template <int NA>
 __device__ __forceinline__ void dense_col_dots(const float* L, int n, int j, int lane, float* out) {
-  float a0[NA], a1[NA];
+  float a0[NA], a1[NA], a2[NA], a3[NA];
   int ro[NA];
 #pragma unroll
   for (int s = 0; s < NA; ++s) {
-    a0[s] = 0.f;
-    a1[s] = 0.f;
+    a0[s] = a1[s] = a2[s] = a3[s] = 0.f;
     const int i = j + 1 + lane + 32 * s;
     ro[s] = i < n ? i : j;            // rows past the end read row j (in bounds) and are dropped
   }
   int cb = 0;                         // column p starts at cb + p
   int p = 0;
-  for (; p + 1 < j; p += 2) {
-    const int cb1 = cb + n - p - 1;
-    const float l0 = L[cb + j], l1 = L[cb1 + j];
+  // four columns per pass (four independent partial sums)
+  for (; p + 3 < j; p += 4) {
+    const int cb1 = cb + n - p - 1, cb2 = cb1 + n - p - 2, cb3 = cb2 + n - p - 3;
+    const float l0 = L[cb + j], l1 = L[cb1 + j], l2 = L[cb2 + j], l3 = L[cb3 + j];
 #pragma unroll
     for (int s = 0; s < NA; ++s) {
       a0[s] = fmaf(L[cb + ro[s]], l0, a0[s]);
       a1[s] = fmaf(L[cb1 + ro[s]], l1, a1[s]);
+      a2[s] = fmaf(L[cb2 + ro[s]], l2, a2[s]);
+      a3[s] = fmaf(L[cb3 + ro[s]], l3, a3[s]);
     }
-    cb = cb1 + n - p - 2;
+    cb = cb3 + n - p - 4;
   }
-  if (p < j) {
+  for (; p < j; ++p) {
     const float l0 = L[cb + j];
 #pragma unroll
     for (int s = 0; s < NA; ++s) a0[s] = fmaf(L[cb + ro[s]], l0, a0[s]);
+    cb += n - p - 1;
   }
 #pragma unroll
-  for (int s = 0; s < NA; ++s) out[s] = a0[s] + a1[s];
+  for (int s = 0; s < NA; ++s) out[s] = (a0[s] + a1[s]) + (a2[s] + a3[s]);
 }
 
 template <int NS>

@@ -555,17 +555,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             sa_next = s4;
           }
         }
-        // chunks of kCc columns; the TMEM load of the next chunk is in flight
-        // while this one is processed
-        constexpr int kNch = C::kCols / kCc;
-        float vb[2][kCc];
-        tmem_ld16f(lane_addr + c0, vb[0]);
-#pragma unroll
-        for (int ci = 0; ci < kNch; ++ci) {
-          const int col = c0 + ci * kCc;
+        for (int cc = 0; cc < C::kCols; cc += kCc) {
+          const int col = c0 + cc;
+          float v[kCc];
+          tmem_ld16f(lane_addr + col, v);
           tmem_wait_ld();
-          if (ci + 1 < kNch) tmem_ld16f(lane_addr + col + kCc, vb[(ci + 1) & 1]);
-          float* v = vb[ci & 1];
           if constexpr (F8) {
 #pragma unroll
             for (int i = 0; i < kCc; ++i) v[i] *= sa * sw[col + i];

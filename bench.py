@@ -123,6 +123,13 @@ def launches_per_step(whiten: bool) -> int:
     return 5 + 1 + 1 + (22 if whiten else 0) + 5
 
 
+# DRAM bytes (read + write) per unique pair of the BF16 tensor-core MLP kernel, from
+# one ncu capture of the 100k-event step (8.39 MB read + 2.6 KB written for about
+# 0.372 M pairs; profiles/k_tt_mlp_tc_bf16_100kev.md); scaled by the pairs of a
+# launch.  Only valid while that kernel is unchanged.
+MLP_BF16_DRAM_BYTES_PER_PAIR = (8.391680e6 + 2.56e3) / 372371.5
+
+
 def flops_per_pair(H: int) -> float:
     # forward 3 H x H layers + 6 -> H + H -> 1, reverse 3 H x H layers + H -> 3
     return 12.0 * H * H + 20.0 * H
@@ -214,8 +221,10 @@ def run_ours(args, rank, world):
                 "kernel": "k_tt_mlp_fp32<256>", "peak_source": "152 SMs x 128 FP32 lanes x 2 x max clock"}
     else:
         peak = pk["bf16_tflops_sustained"] * (2.0 if args.precision == "fp8" else 1.0)
+        traffic = (MLP_BF16_DRAM_BYTES_PER_PAIR * p_per_step
+                   if args.precision == "bf16" and args.workload in (3, 4) else None)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": "k_tt_mlp_tc",
                 "peak_source": (f"bf16 sustained x 2 (nominal fp8/bf16 dense ratio), {which}"
                                 if args.precision == "fp8" else f"bf16 sustained, {which}")}

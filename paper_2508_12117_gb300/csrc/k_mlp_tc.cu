@@ -234,6 +234,44 @@ __device__ __forceinline__ void silu_tc(float z, float& h, float& d) {
   d = fmaf(z * s, 1.0f - s, s);
 }
 
+// two FP32 lanes per instruction (f32x2): the same IEEE operations as the scalar
+// forms, so results are identical to them
+__device__ __forceinline__ uint64_t f2pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+constexpr uint64_t kHalf2 = 0x3F0000003F000000ull;    // (0.5, 0.5)
+constexpr uint64_t kOne2 = 0x3F8000003F800000ull;     // (1, 1)
+constexpr uint64_t kMinus2 = 0xBF800000BF800000ull;   // (-1, -1)
+
+// silu_tc on two values: h = z s, d = s + h (1 - s), s = (1 + tanh(z/2)) / 2
+__device__ __forceinline__ void silu_pair(uint64_t z, uint64_t& h, uint64_t& d) {
+  float a, b;
+  f2unpack(f2mul(z, kHalf2), a, b);
+  const uint64_t s = f2fma(f2pack(tanh_fast(a), tanh_fast(b)), kHalf2, kHalf2);
+  h = f2mul(z, s);
+  d = f2fma(h, f2fma(s, kMinus2, kOne2), s);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
@@ -332,7 +370,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = threadIdx.x; i < 6 * H; i += blockDim.x) pW1[i] = net.W1[i];
+  // W1 transposed in shared memory (6 x H: input c, column) so that column pairs are adjacent
+  for (int i = threadIdx.x; i < 6 * H; i += blockDim.x) pW1[(i % 6) * H + i / 6] = net.W1[i];
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
     pb1[i] = net.b1[i];
     pb[i] = net.bh[0][i];
@@ -463,6 +502,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         x[c] = gb[c * kRows + r] + (gb[(3 + c) * kRows + r] + gb[(6 + c) * kRows + r]);
         x[3 + c] = gb[(9 + c) * kRows + r] + gb[(12 + c) * kRows + r];
       }
+      uint64_t x2[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) x2[c] = f2pack(x[c], x[c]);
       float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
       bool ok = true;
       float sa = 1.f;                                  // FP8: dequantisation scale of this A row
@@ -475,7 +517,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int col = c0 + cc;
             float z = pb1[col];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) z = fmaf(pW1[col * 6 + c], x[c], z);
+            for (int c = 0; c < 6; ++c) z = fmaf(pW1[c * H + col], x[c], z);
             m = fmaxf(m, z);
           }
           const bool got = group_max(m, xch, &xbar[g], xph, cg, r, abort_flag, gerr);
@@ -489,15 +531,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           uint32_t dp[kCc / 2];
 #pragma unroll
           for (int i = 0; i < kCc; i += 2) {
-            float z0 = pb1[col + i], z1 = pb1[col + i + 1];
+            uint64_t z = *reinterpret_cast<const uint64_t*>(pb1 + col + i);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-              z0 = fmaf(pW1[(col + i) * 6 + c], x[c], z0);
-              z1 = fmaf(pW1[(col + i + 1) * 6 + c], x[c], z1);
-            }
+            for (int c = 0; c < 6; ++c)
+              z = f2fma(*reinterpret_cast<const uint64_t*>(pW1 + c * H + col + i), x2[c], z);
+            uint64_t hh, dd2;
+            silu_pair(z, hh, dd2);
             float d0, d1;
-            silu_tc(z0, h[i], d0);
-            silu_tc(z1, h[i + 1], d1);
+            f2unpack(hh, h[i], h[i + 1]);
+            f2unpack(dd2, d0, d1);
             dp[i / 2] = pack_bf16(d0, d1);
           }
           if constexpr (F8) {
@@ -571,15 +613,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t dp[kCc / 2];
 #pragma unroll
             for (int i = 0; i < kCc; i += 2) {
+              uint64_t hh, dd2;
+              silu_pair(f2add(f2pack(v[i], v[i + 1]), *reinterpret_cast<const uint64_t*>(bias + col + i)), hh, dd2);
               float h0, d0, h1, d1;
-              silu_tc(v[i] + bias[col + i], h0, d0);
-              silu_tc(v[i + 1] + bias[col + i + 1], h1, d1);
+              f2unpack(hh, h0, h1);
               if (layer == 2) {
-                const float w0 = pw5[col + i], w1 = pw5[col + i + 1];
+                const uint64_t w = *reinterpret_cast<const uint64_t*>(pw5 + col + i);
+                float w0, w1;
+                f2unpack(w, w0, w1);
                 tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
-                o[i] = w0 * d0;                        // delta4
-                o[i + 1] = w1 * d1;
+                f2unpack(f2mul(w, dd2), o[i], o[i + 1]);          // delta4
               } else {
+                f2unpack(dd2, d0, d1);
                 o[i] = h0;
                 o[i + 1] = h1;
                 dp[i / 2] = pack_bf16(d0, d1);
@@ -604,15 +649,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               tmem_wait_ld();
             }
 #pragma unroll
-            for (int i = 0; i < kCc; i += 2) {
-              o[i] = v[i] * bf16_lo(dd[i / 2]);
-              o[i + 1] = v[i + 1] * bf16_hi(dd[i / 2]);
-            }
+            for (int i = 0; i < kCc; i += 2)
+              f2unpack(f2mul(f2pack(v[i], v[i + 1]), f2pack(bf16_lo(dd[i / 2]), bf16_hi(dd[i / 2]))), o[i],
+                       o[i + 1]);
             if (layer == 5) {
+              // dtau/dx_s: W1[:, :3]^T delta1, column pairs in two lanes
+              uint64_t g2[3] = {0, 0, 0};
 #pragma unroll
-              for (int i = 0; i < kCc; ++i)
+              for (int i = 0; i < kCc; i += 2) {
+                const uint64_t e2 = f2pack(o[i], o[i + 1]);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) gpart[c] = fmaf(pW1[(col + i) * 6 + c], o[i], gpart[c]);
+                for (int c = 0; c < 3; ++c)
+                  g2[c] = f2fma(*reinterpret_cast<const uint64_t*>(pW1 + c * H + col + i), e2, g2[c]);
+              }
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                float a, b;
+                f2unpack(g2[c], a, b);
+                gpart[c] += a + b;
+              }
             }
           }
           if (layer < 5) {

@@ -479,9 +479,11 @@ __global__ void k_cc_local(StepView v) {
     }
     if (mine) changed = 1;
     __syncthreads();
+    // every thread takes the flag before the next round's reset can overwrite it
+    const int any = changed;
     for (int l = threadIdx.x; l < L; l += blockDim.x) par[l] = lroot_find(par, l);
     __syncthreads();
-    if (!changed) break;
+    if (!any) break;
     if (round == 63 && threadIdx.x == 0) set_error(v.counters, SPIDER_E_TIMEOUT);
   }
   for (int l = threadIdx.x; l < L; l += blockDim.x) v.cc_lroot[q0 + l] = q0 + par[l];

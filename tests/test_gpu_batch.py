@@ -78,3 +78,55 @@ def test_batch_minibatch_matches_oracle(cats):
             off += cat.M
             sub += 1
     bat.close()
+
+
+def test_batch_minibatch_matches_single_contexts(cats):
+    # sub-problem s of the batch draws its blocks with key seed ^ (s * golden): a
+    # single context stepped with that key walks the identical chain, bit for bit
+    # (noise off: the batch keys its noise with the untransformed seed)
+    chains = 2
+    net = binding.Net(binding.TT_HOMOGENEOUS, v0=6.0)
+    B, bn = 512, 1500
+    cfg = binding.make_config(sigma=0.01, kappa=0.03, batch_n=bn, block_obs=B, thin=1, sample_cap=1,
+                              noise_scale=0.0)
+    bat = binding.Context.batch(cats, chains, net, cfg)
+    seeds = [31, 32, 33, 34]
+    for s in seeds:
+        bat.spider_sgld_step(1e-5, s)
+    th_b, _ = bat.spider_get_state()
+    off, sub = 0, 0
+    for ci, cat in enumerate(cats):
+        for h in range(chains):
+            ctx = binding.Context(cat.init_xyzt, cat.i, cat.j, cat.k, cat.dt, cat.stations, net,
+                                  binding.make_config(sigma=0.01, kappa=0.03, batch_n=bn, block_obs=B,
+                                                      chain=h, catalog=ci, thin=1, sample_cap=1,
+                                                      noise_scale=0.0))
+            for s in seeds:
+                ctx.spider_sgld_step(1e-5, (s ^ ((GOLDEN * sub) & 0xFFFFFFFFFFFFFFFF)) & 0xFFFFFFFFFFFFFFFF)
+            th, _ = ctx.spider_get_state()
+            assert np.array_equal(th_b[off:off + cat.M], th), (ci, h)
+            ctx.close()
+            off += cat.M
+            sub += 1
+    bat.close()
+
+
+def test_batched_mlp_workload_stays_finite():
+    # the 16-catalog x 4-chain workload with the BF16 network: 25 steps stay finite
+    # and every sub-problem moves by less than the prior width allows
+    specs = synth.batch_specs(16)
+    cats16 = [synth.make_catalog(s) for s in specs]
+    h = specs[0].hyper
+    net = binding.Net(binding.TT_MLP, mlp=synth.batch_network())
+    cfg = binding.make_config(sigma=h.sigma, kappa=h.kappa, p=h.p, ell=h.ell, eps_w=h.eps_w,
+                              sig_e=h.sig_e, sig_c=h.sig_c, batch_n=h.batch_n, block_obs=h.block_obs,
+                              precision=binding.BF16, thin=1, sample_cap=1)
+    bat = binding.Context.batch(cats16, 4, net, cfg)
+    th0, _ = bat.spider_get_state()
+    for s in range(25):
+        bat.spider_sgld_step(h.eps, 100 + s)
+    th, _ = bat.spider_get_state()
+    move = np.abs(th - th0)[:, :3].max()
+    print(f"batched workload, 25 steps: max move {move:.3f} km")
+    assert np.isfinite(th).all() and move < 10.0
+    bat.close()

@@ -119,8 +119,8 @@ def build_workload(wid: int):
 
 def launches_per_step(whiten: bool) -> int:
     # selection + pair table 5, travel times 1, residuals 1, whitening (CSR
-    # assembly 4, components 11, work list 2, solvers 3 + merge 1), scatter/update 5
-    return 5 + 1 + 1 + (22 if whiten else 0) + 5
+    # assembly 4, components 15, work list 2, solvers 3 + merge 1), scatter/update 5
+    return 5 + 1 + 1 + (26 if whiten else 0) + 5
 
 
 # DRAM bytes (read + write) per unique pair of the BF16 tensor-core MLP kernel, from

@@ -530,6 +530,8 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   AL(big, PP);
   AL(chist, 512);
   AL(cc_lroot, Q);
+  AL(bigpos, PP + 1);
+  AL(biglist, PP);
   AL(corder, PP);
   AL(centries, PP);
   AL(ctier, PP);

@@ -427,7 +427,7 @@ __global__ void k_fill_rows(StepView v) {
 constexpr int kCcRounds = 64;
 constexpr int kCompMax = 256;        // largest component solved by one warp
 constexpr int kCompEnt = 3072;       // largest CSR entry count cached by one warp
-constexpr int kCtaMax = 8192;        // largest component solved by one CTA
+constexpr int kCtaMax = 1024;        // largest component solved by one CTA (larger: grid-wide CG)
 constexpr int kCqBins = kCompMax + 1;   // work-list bins (see k_corder_scan)
 
 __device__ __forceinline__ int32_t cc_root(const int32_t* lab, int32_t u) {
@@ -577,11 +577,20 @@ __global__ void k_cc_place(StepView v) {
     const int32_t n = v.comp_off[c + 1] - v.comp_off[c];
     const int tier = (n <= kCompMax && v.centries[c] <= kCompEnt) ? 0 : (n <= kCtaMax ? 1 : 2);
     v.big[u] = tier == 2 ? 1 : 0;
+    v.bigpos[u] = tier == 2 ? 1 : 0;
     if (u == v.comp_root[c]) {
       v.ctier[c] = (uint8_t)tier;
       if (tier < 2) atomicAdd(&v.chist[tier == 1 ? 0 : 1 + (kCompMax - n)], 1);
     }
   }
+}
+
+// the nodes of the grid-tier components as a list in pair order (bigpos holds
+// their exclusive prefix)
+__global__ void k_big_list(StepView v) {
+  const int32_t P_u = v.counters[kCntPairs];
+  for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x)
+    if (v.big[u]) v.biglist[v.bigpos[u]] = u;
 }
 
 __device__ __forceinline__ float warp_allsum(float x) {
@@ -1432,10 +1441,10 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
   const float lam = v.lam;
   constexpr float kInnerTol = 1e-3f;
   constexpr int kMaxRounds = 8;
-  const uint8_t* big = v.big;
+  const int32_t nbig = v.bigpos[P_u];      // nodes of the grid-tier components, in pair order
   float bb = 0.f;
-  for (int32_t u = gtid; u < P_u; u += gstride) {
-    if (!big[u]) continue;
+  for (int32_t t = gtid; t < nbig; t += gstride) {
+    const int32_t u = v.biglist[t];
     const float r = v.rhs[u];
     v.z[u] = 0.f;
     v.z_lo[u] = 0.f;
@@ -1450,8 +1459,8 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
   for (int round = 0; round < kMaxRounds && bb > 0.f && it < max_it; ++round) {
     // outer residual u - A z in double-float; inner start: res = y = D^-1 res
     float rz = 0.f, rr0 = 0.f;
-    for (int32_t u = gtid; u < P_u; u += gstride) {
-      if (!big[u]) continue;
+    for (int32_t t = gtid; t < nbig; t += gstride) {
+      const int32_t u = v.biglist[t];
       float r;
       if (round == 0) {
         r = v.rhs[u] + v.rhs_lo[u];
@@ -1490,8 +1499,8 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
     while (it < max_it) {
       // p = y + beta p;  A p = A y + beta A p;  p.Ap
       float dot = 0.f;
-      for (int32_t u = gtid; u < P_u; u += gstride) {
-        if (!big[u]) continue;
+      for (int32_t t = gtid; t < nbig; t += gstride) {
+        const int32_t u = v.biglist[t];
         const float yu = v.yv[u];
         float s = 0.f;
         for (int32_t t = v.rowptr[u], t1 = v.rowptr[u + 1]; t < t1; ++t) {
@@ -1511,8 +1520,8 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
       const float pap = sum_partials(red + 2 * kMaxGrid, G, smr);
       const float alpha = pap > 0.f ? rz / pap : 0.f;
       float rzn = 0.f, rr = 0.f;
-      for (int32_t u = gtid; u < P_u; u += gstride) {
-        if (!big[u]) continue;
+      for (int32_t t = gtid; t < nbig; t += gstride) {
+        const int32_t u = v.biglist[t];
         v.dz[u] = fmaf(alpha, v.pv[u], v.dz[u]);
         const float r = fmaf(-alpha, v.Ap[u], v.res[u]);
         v.res[u] = r;
@@ -1537,8 +1546,8 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
       first = false;
     }
     // z += dz in double-float; the next round reads z at neighbours
-    for (int32_t u = gtid; u < P_u; u += gstride) {
-      if (!big[u]) continue;
+    for (int32_t t = gtid; t < nbig; t += gstride) {
+      const int32_t u = v.biglist[t];
       const df32 zn = df_add_f(df32{v.z[u], v.z_lo[u]}, v.dz[u]);
       v.z[u] = zn.hi;
       v.z_lo[u] = zn.lo;
@@ -1894,6 +1903,10 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
   k_scan_c<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part, v.comp_off);
   k_cc_fill<<<parts, kThreads, 0, st>>>(v);
   k_cc_place<<<parts, kThreads, 0, st>>>(v);
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.bigpos, Pdev, v.scan_part);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.bigpos, Pdev, v.scan_part, v.bigpos);
+  k_big_list<<<parts, kThreads, 0, st>>>(v);
   k_corder_scan<<<1, 512, 0, st>>>(v);
   k_corder_fill<<<parts, kThreads, 0, st>>>(v);
   // the CTA tier first; the warp tier may start as soon as every CTA of it has

@@ -163,6 +163,8 @@ struct StepView {
   int32_t* lidx;       // [P] local index of a member inside its component
   uint8_t* big;        // [P] 1: the row belongs to a component solved by the grid-wide CG
   int32_t* chist;      // [kCqBins + 4] solver work-list bins and cursors
+  int32_t* bigpos;     // [P + 1] exclusive prefix of the grid-tier flags (then the count)
+  int32_t* biglist;    // [P] grid-tier nodes in pair order
   int32_t* cc_lroot;   // [Q] per local node of a selected block: its block-local component root (local node id)
   int32_t* corder;     // [P] solver work list (component ids)
   int32_t* centries;   // [P] CSR entries per component

@@ -124,10 +124,10 @@ def launches_per_step(whiten: bool) -> int:
 
 
 # DRAM bytes (read + write) per unique pair of the BF16 tensor-core MLP kernel, from
-# one ncu capture of the 100k-event step (8.39 MB read + 2.6 KB written for about
-# 0.372 M pairs; profiles/k_tt_mlp_tc_bf16_100kev.md); scaled by the pairs of a
-# launch.  Only valid while that kernel is unchanged.
-MLP_BF16_DRAM_BYTES_PER_PAIR = (8.391680e6 + 2.56e3) / 372371.5
+# one ncu capture of the 100k-event step (8.39 MB read, nothing written back to
+# DRAM, for about 0.372 M pairs; profiles/k_tt_mlp_tc_bf16_100kev.md); scaled by the
+# pairs of a launch.  Only valid while that kernel is unchanged.
+MLP_BF16_DRAM_BYTES_PER_PAIR = 8.388608e6 / 372371.5
 
 
 def flops_per_pair(H: int) -> float:

@@ -62,8 +62,9 @@ enum {
 enum { SPIDER_FP32 = 0, SPIDER_BF16 = 1, SPIDER_FP8 = 2 };
 
 typedef struct {
-  int64_t M;               /* events                                             */
-  int64_t N;               /* dd observations                                    */
+  int64_t M;               /* events, 2 <= M < 2^31                              */
+  int64_t N;               /* dd observations, 1 <= N < 2^30 (a double difference
+                              needs two events and at least one observation)     */
   const double *xyzt0;     /* M x 4 row-major initial catalog theta_0: x, y, z (km,
                               z positive down), t0 (s).  Also the mean of the event
                               prior (Sec. 3.1) and the centre of the centroid prior. */
@@ -140,7 +141,9 @@ void spider_config_default(spider_config *cfg);
 /* Validates and copies the catalog, stations and network; builds the canonical
  * observation order, the (event, station) pair table, the minibatch blocks and
  * the edge weights; uploads everything; state theta := theta_0, step := 0.
- * stream: a cudaStream_t or NULL.  *out receives the context on success. */
+ * stream: a cudaStream_t or NULL.  *out receives the context on success.
+ * SPIDER_E_INVAL (with a message) for sizes out of range, indices out of range,
+ * i == j, non-finite coordinates or times, or an invalid configuration. */
 int spider_create(const spider_catalog *cat, const spider_stations *sta,
                   const spider_net *net, const spider_config *cfg, void *stream,
                   spider_ctx **out);

@@ -327,6 +327,16 @@ def test_invalid_inputs_rejected(cat1):
     assert e.value.code == -1
     with pytest.raises(binding.SpiderError):
         binding.Context.from_catalog(cat1, block_obs=5000)
+    # degenerate sizes: no observation, a single event
+    net = binding.net_for_catalog(cat1)
+    cfg = binding.config_for_catalog(cat1)
+    with pytest.raises(binding.SpiderError) as e:
+        binding.Context(cat1.init_xyzt, cat1.i[:0], cat1.j[:0], cat1.k[:0], cat1.dt[:0], cat1.stations, net, cfg)
+    assert e.value.code == -1
+    with pytest.raises(binding.SpiderError) as e:
+        binding.Context(cat1.init_xyzt[:1], np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros(1, np.int32),
+                        np.zeros(1), cat1.stations, net, cfg)
+    assert e.value.code == -1
 
 
 def test_two_event_catalog():

@@ -426,7 +426,7 @@ __global__ void k_fill_rows(StepView v) {
 // compression until a round hooks nothing.
 constexpr int kCcRounds = 64;
 constexpr int kCompMax = 256;        // largest component solved by one warp
-constexpr int kCompEnt = 3072;       // largest CSR entry count cached by one warp
+constexpr int kCompEnt = 2048;       // largest CSR entry count cached by one warp
 constexpr int kCtaMax = 1024;        // largest component solved by one CTA (larger: grid-wide CG)
 constexpr int kCqBins = kCompMax + 1;   // work-list bins (see k_corder_scan)
 
@@ -690,10 +690,10 @@ __global__ void k_corder_fill(StepView v) {
 // factorised (dense Cholesky, FP32) and z refined with the double-float
 // residual; otherwise (or when the factorisation fails) the same refinement
 // takes Jacobi-CG corrections to 1e-3.
-constexpr int kCompWarps = 4;
-constexpr int kDenseMax = 96;
+constexpr int kCompWarps = 2;
+constexpr int kDenseMax = 80;
 constexpr int kDenseEnt = 640;
-constexpr int kDenseSlots = kDenseMax / 32;
+constexpr int kDenseSlots = (kDenseMax + 31) / 32;
 
 struct WarpSmem {
   int32_t mu[kCompMax];              // sorted members, padded to a power of two
@@ -1914,7 +1914,7 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
   k_comp_solve_cta<<<cta_mult * parts, kCtaThreads, sizeof(CtaSmem), st>>>(v, max_it, tol);
   {
     cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)(warp_mult * parts));
+    lc.gridDim = dim3((unsigned)(warp_mult * parts * (4 / kCompWarps)));   // the same warps for any CTA size
     lc.blockDim = dim3(kCompWarps * 32);
     lc.dynamicSmemBytes = kCompWarps * sizeof(WarpSmem);
     lc.stream = st;

@@ -426,7 +426,7 @@ __global__ void k_fill_rows(StepView v) {
 // compression until a round hooks nothing.
 constexpr int kCcRounds = 64;
 constexpr int kCompMax = 256;        // largest component solved by one warp
-constexpr int kCompEnt = 2048;       // largest CSR entry count cached by one warp
+constexpr int kCompEnt = 1664;       // largest CSR entry count cached by one warp
 constexpr int kCtaMax = 1024;        // largest component solved by one CTA (larger: grid-wide CG)
 constexpr int kCqBins = kCompMax + 1;   // work-list bins (see k_corder_scan)
 
@@ -691,7 +691,7 @@ __global__ void k_corder_fill(StepView v) {
 // residual; otherwise (or when the factorisation fails) the same refinement
 // takes Jacobi-CG corrections to 1e-3.
 constexpr int kCompWarps = 2;
-constexpr int kDenseMax = 80;
+constexpr int kDenseMax = 72;
 constexpr int kDenseEnt = 640;
 constexpr int kDenseSlots = (kDenseMax + 31) / 32;
 

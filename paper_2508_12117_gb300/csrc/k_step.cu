@@ -425,8 +425,9 @@ __global__ void k_fill_rows(StepView v) {
 // the order of the atomics.  Rounds alternate hooking and full path
 // compression until a round hooks nothing.
 constexpr int kCcRounds = 64;
-constexpr int kCompMax = 256;        // largest component solved by one warp
-constexpr int kCompEnt = 1664;       // largest CSR entry count cached by one warp
+constexpr int kCompMax = 192;        // largest component solved by one warp
+constexpr int kCompPad = 256;        // kCompMax rounded up to a power of two (sort padding)
+constexpr int kCompEnt = 1280;       // largest CSR entry count cached by one warp
 constexpr int kCtaMax = 1024;        // largest component solved by one CTA (larger: grid-wide CG)
 constexpr int kCqBins = kCompMax + 1;   // work-list bins (see k_corder_scan)
 
@@ -691,13 +692,15 @@ __global__ void k_corder_fill(StepView v) {
 // residual; otherwise (or when the factorisation fails) the same refinement
 // takes Jacobi-CG corrections to 1e-3.
 constexpr int kCompWarps = 2;
-constexpr int kDenseMax = 72;
+constexpr int kDenseMax = 64;
 constexpr int kDenseEnt = 640;
 constexpr int kDenseSlots = (kDenseMax + 31) / 32;
 
+static_assert(kCompPad >= kCompMax && kCompPad <= 2 * kCompMax, "sort padding of the warp tier");
+
 struct WarpSmem {
-  int32_t mu[kCompMax];              // sorted members, padded to a power of two
-  int32_t lrp[kCompMax + 1];         // local row pointers, padded
+  int32_t mu[kCompPad];              // sorted members, padded to a power of two
+  int32_t lrp[kCompPad + 1];         // local row pointers, padded
   uint8_t perm[kCompMax];            // iterative path: rows by decreasing length
   union {
     struct {
@@ -1002,7 +1005,8 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
     {
       // row order by decreasing length, so that the lanes of a 32-row slot
       // run inner loops of similar trip counts
-      int32_t* key = reinterpret_cast<int32_t*>(rs);
+      // n2 <= kCompPad <= 2 kCompMax entries: vec[3] continues into vec[4] (unused yet)
+      int32_t* key = reinterpret_cast<int32_t*>(S.it.vec[3]);
       for (int i = lane; i < n2; i += 32) key[i] = i < n ? ((S.lrp[i + 1] - S.lrp[i]) << 8 | i) : -1;
       __syncwarp();
       warp_sort(key, n2, lane);

@@ -1125,7 +1125,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
 // entries the component's CSR and vectors live in shared memory (local column
 // indices, two-value reductions with one barrier); larger components keep
 // their vectors in global memory, indexed by unique pair.
-constexpr int kCtaThreads = 512;
+constexpr int kCtaThreads = 256;
 constexpr int kCtaSm = 1024;
 constexpr int kCtaSmEnt = 11264;
 

@@ -52,6 +52,9 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kCc = 16;                     // columns per epilogue chunk
 constexpr int kTcThreads = kEpiThreads + 96;   // + producer, MMA issuer, geometry warps
 constexpr int kStages = 3;
+// mbarriers: full, empty [kStages]; acc_ready, a_ready, drain, red_ready; xbar [4];
+// geo_full, geo_empty [2]
+constexpr int kBars = 2 * kStages + 4 + 4 + 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 template <int H, bool F8>
@@ -74,7 +77,7 @@ struct Cfg {
   static constexpr int oRed = oXch + (F8 ? 2 * kGroups * kRows * 4 : 0);   // [4][kGroups][kRows] floats
   static constexpr int oGeo = oRed + 4 * kGroups * kRows * 4;   // pair geometry [2][15][kRows] floats
   static constexpr int oBar = oGeo + 2 * 15 * kRows * 4;         // mbarriers
-  static constexpr int oMisc = oBar + 16 * 8;             // tmem base, abort flag
+  static constexpr int oMisc = oBar + kBars * 8;          // tmem base, abort flag
   static constexpr int kSmem = oMisc + 16 + 1024;         // + alignment slack
 };
 

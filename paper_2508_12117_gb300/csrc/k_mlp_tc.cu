@@ -19,7 +19,16 @@
 //              K = 16, A = activations (SW128 K-major, shared memory),
 //              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
 // TMEM (2H columns): [0, H) accumulator, [H, 3H/2) silu'(z1) and [3H/2, 2H)
-// silu'(z2) packed as BF16 pairs; silu'(z3) sits in shared memory.
+// silu'(z2) packed as BF16 pairs; silu'(z3) sits in a per-CTA global slot.  At
+// the end of a tile the first 16 columns of the silu'(z2) region (last read by
+// the layer-4 epilogue, which every thread has left before the layer-5 product
+// starts) carry the column groups' partial sums of tau and dtau/dx to the
+// row's first column group.
+// Four weight stages hold a whole layer at H = 256 (BF16), so the next layer's
+// weights are resident when its operand is ready.
+// Shared memory keeps W1 and the biases pre-halved (exact): the epilogue works
+// with u = z/2, silu(z) = u + u tanh(u), silu'(z) = s + silu(z) (1 - s),
+// s = (1 + tanh(u)) / 2.
 // FP8 form (kind::f8f6f4, E4M3 operands, FP32 accumulation): the weight images
 // carry one scale per output column (max |W| / 448); each activation row is
 // quantised with its own scale, from a first pass over the accumulator that
@@ -51,7 +60,7 @@ constexpr int kGroups = kEpiWarps / 4;     // column groups per TMEM lane quarte
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kCc = 16;                     // columns per epilogue chunk
 constexpr int kTcThreads = kEpiThreads + 96;   // + producer, MMA issuer, geometry warps
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 // mbarriers: full, empty [kStages]; acc_ready, a_ready, drain, red_ready; xbar [4];
 // geo_full, geo_empty [2]
 constexpr int kBars = 2 * kStages + 4 + 4 + 4;
@@ -74,11 +83,11 @@ struct Cfg {
   static constexpr int oPar = oB + kStages * kChunk;      // W1 (6H), b1, b2, b3, b4, w5 (5H) floats
   static constexpr int oSc = oPar + 11 * H * 4;           // FP8: column scales of the 6 images (6H floats)
   static constexpr int oXch = oSc + (F8 ? 6 * H * 4 : 0); // FP8: row-bound exchange [2][kGroups][kRows] floats
-  static constexpr int oRed = oXch + (F8 ? 2 * kGroups * kRows * 4 : 0);   // [4][kGroups][kRows] floats
-  static constexpr int oGeo = oRed + 4 * kGroups * kRows * 4;   // pair geometry [2][15][kRows] floats
+  static constexpr int oGeo = oXch + (F8 ? 2 * kGroups * kRows * 4 : 0);   // pair geometry [2][15][kRows] floats
   static constexpr int oBar = oGeo + 2 * 15 * kRows * 4;         // mbarriers
   static constexpr int oMisc = oBar + kBars * 8;          // tmem base, abort flag
   static constexpr int kSmem = oMisc + 16 + 1024;         // + alignment slack
+  static_assert(kSmem <= 232448, "shared memory per CTA");
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -207,6 +216,11 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+               "r"(r[2]), "r"(r[3])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
@@ -264,15 +278,16 @@ __device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
 }
 constexpr uint64_t kHalf2 = 0x3F0000003F000000ull;    // (0.5, 0.5)
 constexpr uint64_t kOne2 = 0x3F8000003F800000ull;     // (1, 1)
-constexpr uint64_t kMinus2 = 0xBF800000BF800000ull;   // (-1, -1)
+constexpr uint64_t kNegHalf2 = 0xBF000000BF000000ull;  // (-0.5, -0.5)
 
-// silu_tc on two values: h = z s, d = s + h (1 - s), s = (1 + tanh(z/2)) / 2
-__device__ __forceinline__ void silu_pair(uint64_t z, uint64_t& h, uint64_t& d) {
+// silu and silu' of z = 2u on two values: t = tanh(u), h = u + u t,
+// d = s + h (1 - s) with s = (1 + t) / 2 and 1 - s = (1 - t) / 2
+__device__ __forceinline__ void silu_half(uint64_t u, uint64_t& h, uint64_t& d) {
   float a, b;
-  f2unpack(f2mul(z, kHalf2), a, b);
-  const uint64_t s = f2fma(f2pack(tanh_fast(a), tanh_fast(b)), kHalf2, kHalf2);
-  h = f2mul(z, s);
-  d = f2fma(h, f2fma(s, kMinus2, kOne2), s);
+  f2unpack(u, a, b);
+  const uint64_t t = f2pack(tanh_fast(a), tanh_fast(b));
+  h = f2fma(u, t, u);
+  d = f2fma(h, f2fma(t, kNegHalf2, kHalf2), f2fma(t, kHalf2, kHalf2));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -338,7 +353,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float* pb1 = pW1 + 6 * H;
   float* pb = pb1 + H;       // b2, b3, b4
   float* pw5 = pb + 3 * H;
-  float* red = reinterpret_cast<float*>(sm + C::oRed);
   float* wsc = reinterpret_cast<float*>(sm + C::oSc);     // FP8 column scales [6][H]
   float* xch = reinterpret_cast<float*>(sm + C::oXch);    // FP8 row-bound exchange
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::oBar);
@@ -373,13 +387,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // W1 transposed in shared memory (6 x H: input c, column) so that column pairs are adjacent
-  for (int i = threadIdx.x; i < 6 * H; i += blockDim.x) pW1[(i % 6) * H + i / 6] = net.W1[i];
+  // W1 / 2 transposed in shared memory (6 x H: input c, column) so that column
+  // pairs are adjacent; b1 / 2 .. b4 / 2 (halving is exact)
+  for (int i = threadIdx.x; i < 6 * H; i += blockDim.x) pW1[(i % 6) * H + i / 6] = 0.5f * net.W1[i];
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
-    pb1[i] = net.b1[i];
-    pb[i] = net.bh[0][i];
-    pb[H + i] = net.bh[1][i];
-    pb[2 * H + i] = net.bh[2][i];
+    pb1[i] = 0.5f * net.b1[i];
+    pb[i] = 0.5f * net.bh[0][i];
+    pb[H + i] = 0.5f * net.bh[1][i];
+    pb[2 * H + i] = 0.5f * net.bh[2][i];
     pw5[i] = net.W5[i];
   }
   if constexpr (F8)
@@ -518,10 +533,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           float m = 0.2785f;                           // silu(z) >= -0.2785
           for (int cc = 0; cc < C::kCols; ++cc) {
             const int col = c0 + cc;
-            float z = pb1[col];
+            float u = pb1[col];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) z = fmaf(pW1[c * H + col], x[c], z);
-            m = fmaxf(m, z);
+            for (int c = 0; c < 6; ++c) u = fmaf(pW1[c * H + col], x[c], u);
+            m = fmaxf(m, 2.f * u);
           }
           const bool got = group_max(m, xch, &xbar[g], xph, cg, r, abort_flag, gerr);
           if (!__all_sync(0xffffffffu, got)) break;
@@ -534,12 +549,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           uint32_t dp[kCc / 2];
 #pragma unroll
           for (int i = 0; i < kCc; i += 2) {
-            uint64_t z = *reinterpret_cast<const uint64_t*>(pb1 + col + i);
+            uint64_t u = *reinterpret_cast<const uint64_t*>(pb1 + col + i);
 #pragma unroll
             for (int c = 0; c < 6; ++c)
-              z = f2fma(*reinterpret_cast<const uint64_t*>(pW1 + c * H + col + i), x2[c], z);
+              u = f2fma(*reinterpret_cast<const uint64_t*>(pW1 + c * H + col + i), x2[c], u);
             uint64_t hh, dd2;
-            silu_pair(z, hh, dd2);
+            silu_half(u, hh, dd2);
             float d0, d1;
             f2unpack(hh, h[i], h[i + 1]);
             f2unpack(dd2, d0, d1);
@@ -585,7 +600,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               tmem_wait_ld();
               if (layer <= 1) {
 #pragma unroll
-                for (int i = 0; i < kCc; ++i) m = fmaxf(m, fmaf(v[i], sa * sw[col + i], bias[col + i]));
+                for (int i = 0; i < kCc; ++i) m = fmaxf(m, 2.f * fmaf(v[i] * (sa * sw[col + i]), 0.5f, bias[col + i]));
               } else {
 #pragma unroll
                 for (int i = 0; i < kCc; ++i) m = fmaxf(m, 1.1f * fabsf(v[i] * (sa * sw[col + i])));
@@ -617,7 +632,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
             for (int i = 0; i < kCc; i += 2) {
               uint64_t hh, dd2;
-              silu_pair(f2add(f2pack(v[i], v[i + 1]), *reinterpret_cast<const uint64_t*>(bias + col + i)), hh, dd2);
+              silu_half(f2fma(f2pack(v[i], v[i + 1]), kHalf2, *reinterpret_cast<const uint64_t*>(bias + col + i)), hh,
+                        dd2);
               float h0, d0, h1, d1;
               f2unpack(hh, h0, h1);
               if (layer == 2) {
@@ -669,7 +685,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               for (int c = 0; c < 3; ++c) {
                 float a, b;
                 f2unpack(g2[c], a, b);
-                gpart[c] += a + b;
+                gpart[c] += 2.f * (a + b);                 // W1 is kept halved
               }
             }
           }
@@ -698,25 +714,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
       if (!ok) break;
+      // combine the column groups of each row (fixed order) and write T, dT/dx:
+      // the partial sums go through TMEM columns 3H/2 + [4 cg, 4 cg + 4), next
+      // written by the next tile's layer-2 epilogue (after every thread's
+      // layer-1 arrival)
+      const uint32_t red_addr = lane_addr + (uint32_t)(H + H / 2);
+      {
+        const uint32_t pr[4] = {__float_as_uint(tpart), __float_as_uint(gpart[0]), __float_as_uint(gpart[1]),
+                                __float_as_uint(gpart[2])};
+        tmem_st4(red_addr + (uint32_t)(4 * cg), pr);
+        tmem_wait_st();
+      }
       tc_before();
-      // combine the column groups of each row (fixed order) and write T, dT/dx
-      red[(0 * kGroups + cg) * kRows + r] = tpart;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) red[((1 + c) * kGroups + cg) * kRows + r] = gpart[c];
       mbar_arrive(red_ready);
       const bool got = mbar_wait(red_ready, red_phase, abort_flag, gerr);
       red_phase ^= 1;
       if (!__all_sync(0xffffffffu, got)) break;
+      tc_after();
+      float part[16];
+      if (cg == 0) {
+        tmem_ld16f(red_addr, part);
+        tmem_wait_ld();
+      }
       if (cg == 0 && valid) {
-        float dtau = red[0 * kGroups * kRows + r];
+        float dtau = part[0];
         float gt[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gt[c] = red[((1 + c) * kGroups) * kRows + r];
+        for (int c = 0; c < 3; ++c) gt[c] = part[1 + c];
 #pragma unroll
         for (int q = 1; q < kGroups; ++q) {
-          dtau += red[(0 * kGroups + q) * kRows + r];
+          dtau += part[4 * q];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) gt[c] += red[((1 + c) * kGroups + q) * kRows + r];
+          for (int c = 0; c < 3; ++c) gt[c] += part[4 * q + 1 + c];
         }
         PairGeo pg;
 #pragma unroll

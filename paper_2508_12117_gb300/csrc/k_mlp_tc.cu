@@ -8,9 +8,11 @@
 //       delta4 = w5 * silu'(z4);  delta_{l-1} = (W_l^T delta_l) * silu'(z_{l-1})
 //   dtau/dx = W1[:, :3]^T delta1 (FP32),  dT/dx = tau (x - s)/r + r dtau/dx.
 //
-// One CTA per SM, persistent over tiles; 18 warps:
+// One CTA per SM, persistent over tiles; 19 warps:
 //   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one pair per
-//              lane) and columns [ (w / 4) H/4, (w / 4 + 1) H/4 ), 16 at a time;
+//              lane); within every K-block of the next A operand, column group
+//              w / 4 takes a quarter of the K-block's columns, 16 at a time, so
+//              the K-blocks of A complete one after the other;
 //   warp 16    producer: 1-D bulk async copies (cp.async.bulk) of pre-swizzled
 //              weight K-blocks (H rows x 64 BF16) into a two-stage ring;
 //   warp 18    geometry: loads the (event, station) geometry of the next tile
@@ -18,12 +20,16 @@
 //   warp 17    MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = H,
 //              K = 16, A = activations (SW128 K-major, shared memory),
 //              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
-// TMEM (2H columns): [0, H) accumulator, [H, 3H/2) silu'(z1) and [3H/2, 2H)
-// silu'(z2) packed as BF16 pairs; silu'(z3) sits in a per-CTA global slot.  At
-// the end of a tile the first 16 columns of the silu'(z2) region (last read by
-// the layer-4 epilogue, which every thread has left before the layer-5 product
-// starts) carry the column groups' partial sums of tau and dtau/dx to the
-// row's first column group.
+// TMEM (2H columns): two accumulators, [0, H) for products 0, 2, 4 and [H, 2H)
+// for products 1, 3, 5 (forward W2, W3, W4, reverse W4^T, W3^T, W2^T).  Product
+// l + 1 starts on K-block kb of its operand as soon as the epilogue of product l
+// has written that K-block (one barrier per K-block), into the accumulator the
+// epilogue is not reading; only its last K-block is left when the epilogue
+// finishes.  silu'(z1), silu'(z2), silu'(z3) (BF16) sit in three per-CTA slots
+// in global memory (each thread reads back only what it wrote; the stash loads
+// of a reverse layer are issued before its TMEM load).  At the end of a tile the
+// first 16 columns of [0, H) (last read by the product-4 epilogue) carry the
+// column groups' partial sums of tau and dtau/dx to the row's first group.
 // Four weight stages hold a whole layer at H = 256 (BF16), so the next layer's
 // weights are resident when its operand is ready.
 // Shared memory keeps W1 and the biases pre-halved (exact): the epilogue works
@@ -61,9 +67,10 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kCc = 16;                     // columns per epilogue chunk
 constexpr int kTcThreads = kEpiThreads + 96;   // + producer, MMA issuer, geometry warps
 constexpr int kStages = 4;
-// mbarriers: full, empty [kStages]; acc_ready, a_ready, drain, red_ready; xbar [4];
-// geo_full, geo_empty [2]
-constexpr int kBars = 2 * kStages + 4 + 4 + 4;
+constexpr int kMaxKb = 4;                   // K-blocks per layer at most (H = 256, BF16)
+// mbarriers: full, empty [kStages]; acc_ready, drain, red_ready; a_ready [kMaxKb];
+// xbar [4]; geo_full, geo_empty [2]
+constexpr int kBars = 2 * kStages + 3 + kMaxKb + 4 + 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 template <int H, bool F8>
@@ -73,8 +80,13 @@ struct Cfg {
   static constexpr int kChunk = H * 128;            // bytes of one weight K-block (H rows x 128 B)
   static constexpr int kImage = H * H * EB;         // bytes of one weight image
   static constexpr int kA = kRows * H * EB;         // activations, SW128 K-major
-  static constexpr int kD3 = kRows * H * 2;         // silu'(z3), BF16, per-CTA slot in global memory
+  static constexpr int kD = kRows * H * 2;          // one silu'(z) slot (BF16) in global memory
+  static constexpr int kStash = 3 * kD;             // silu'(z1), silu'(z2), silu'(z3) per CTA
   static constexpr int kCols = H / kGroups;         // columns per epilogue thread
+  static constexpr int kKbCols = H / KB;            // columns of one K-block of A
+  static constexpr int kCpk = kKbCols / kGroups / kCc;   // 16-column chunks per thread and K-block
+  static constexpr int kChunks = kCols / kCc;       // chunks per thread and layer
+  static_assert(KB <= kMaxKb && kChunks == KB * kCpk && kCpk >= 1, "tile shape");
   static constexpr int kTmemCols = 2 * H;
   static constexpr int kChunksPerTile = 6 * KB;
   // shared-memory carve-up (offsets from a 1024-aligned base)
@@ -334,8 +346,8 @@ __device__ __forceinline__ bool group_max(float& m, float* xch, uint64_t* xbar, 
   return got;
 }
 
-// silu'(z3): 16-byte chunk c/8 of row r at ((c/8) * 128 + r) * 16
-__device__ __forceinline__ uint32_t d3_off(int r, int c) { return (uint32_t)(((c >> 3) * kRows + r) * 16); }
+// silu'(z) slot: 16-byte chunk c/8 of row r at ((c/8) * 128 + r) * 16
+__device__ __forceinline__ uint32_t d_off(int r, int c) { return (uint32_t)(((c >> 3) * kRows + r) * 16); }
 
 template <int H, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -346,9 +358,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm + C::oA;
   uint8_t* sB = sm + C::oB;
-  // silu'(z3) of the current tile: this CTA's slot in global memory (each thread
-  // reads back only what it wrote)
-  uint8_t* sD3 = stash + (size_t)blockIdx.x * C::kD3;
+  // silu'(z1..3) of the current tile: this CTA's slots in global memory (each
+  // thread reads back only what it wrote)
+  uint8_t* sD = stash + (size_t)blockIdx.x * C::kStash;
   float* pW1 = reinterpret_cast<float*>(sm + C::oPar);
   float* pb1 = pW1 + 6 * H;
   float* pb = pb1 + H;       // b2, b3, b4
@@ -358,13 +370,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::oBar);
   uint64_t* full = bars;                     // [kStages] weight stage loaded
   uint64_t* empty = bars + kStages;          // [kStages] weight stage consumed
-  uint64_t* acc_ready = bars + 2 * kStages;  // accumulator complete
-  uint64_t* a_ready = acc_ready + 1;         // epilogue done with TMEM reads + A written
-  uint64_t* drain = acc_ready + 2;           // MMA drain on abort
-  uint64_t* red_ready = acc_ready + 3;       // every column group of every row reduced
-  uint64_t* xbar = acc_ready + 4;            // [4] FP8 row-bound exchange within a lane quarter
-  uint64_t* geo_full = acc_ready + 8;        // [2] geometry buffer filled
-  uint64_t* geo_empty = acc_ready + 10;      // [2] geometry buffer released by the epilogue
+  uint64_t* acc_ready = bars + 2 * kStages;  // product complete (one phase per product)
+  uint64_t* drain = acc_ready + 1;           // MMA drain on abort
+  uint64_t* red_ready = acc_ready + 2;       // every column group of every row reduced
+  uint64_t* a_ready = acc_ready + 3;         // [kMaxKb] K-block of A written by every epilogue warp
+  uint64_t* xbar = a_ready + kMaxKb;         // [4] FP8 row-bound exchange within a lane quarter
+  uint64_t* geo_full = xbar + 4;             // [2] geometry buffer filled
+  uint64_t* geo_empty = geo_full + 2;        // [2] geometry buffer released by the epilogue
   float* geo = reinterpret_cast<float*>(sm + C::oGeo);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + C::oMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + C::oMisc + 4);
@@ -376,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&empty[q], 1);
     }
     mbar_init(acc_ready, 1);
-    mbar_init(a_ready, kEpiThreads);
+    for (int q = 0; q < kMaxKb; ++q) mbar_init(&a_ready[q], kEpiWarps);
     mbar_init(drain, 1);
     mbar_init(red_ready, kEpiThreads);
     for (int q = 0; q < 4; ++q) mbar_init(&xbar[q], 32 * kGroups);
@@ -470,10 +482,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       int issued = 0;
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
         for (int layer = 0; layer < 6 && ok; ++layer) {
-          if (!mbar_wait(a_ready, a_phase, abort_flag, gerr)) { ok = false; break; }
-          a_phase ^= 1;
-          tc_after();
+          const uint32_t d = tmem + (uint32_t)((layer & 1) * H);     // this product's accumulator
           for (int kb = 0; kb < C::KB; ++kb, ++n) {
+            // K-block kb of the operand written (and the accumulator free: its last
+            // reader, the epilogue two products back, finished before)
+            if (!mbar_wait(&a_ready[kb], a_phase, abort_flag, gerr)) { ok = false; break; }
             const int s = (int)(n % kStages);
             if (!mbar_wait(&full[s], (uint32_t)((n / kStages) & 1), abort_flag, gerr)) { ok = false; break; }
             tc_after();
@@ -481,12 +494,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int k = 0; k < 4; ++k) {
               const uint64_t ad = sw128_desc(a_base + kb * (kRows * 128) + k * 32);
               const uint64_t bd = sw128_desc(b_base + s * C::kChunk + k * 32);
-              umma<F8>(tmem, ad, bd, idesc, (kb | k) ? 1u : 0u);
+              umma<F8>(d, ad, bd, idesc, (kb | k) ? 1u : 0u);
               ++issued;
             }
             umma_commit(&empty[s]);
           }
-          if (ok) umma_commit(acc_ready);
+          if (!ok) break;
+          umma_commit(acc_ready);
+          a_phase ^= 1;
         }
       }
       if (!ok && issued) {
@@ -502,7 +517,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int g = warp & 3, cg = warp >> 2;
     const int r = g * 32 + lane;                       // tile row = TMEM lane
     const uint32_t lane_addr = tmem + ((uint32_t)(g * 32) << 16);
-    const int c0 = cg * C::kCols;                      // first column of this thread
+    // column of this thread's chunk j (K-block-major)
+    auto ccol = [cg](int j) {
+      return (j / C::kCpk) * C::kKbCols + cg * (C::kKbCols / kGroups) + (j % C::kCpk) * kCc;
+    };
+    // this warp's part of K-block kb of the next operand is written (and its TMEM
+    // reads before it are complete)
+    auto a_done = [&](int kb) {
+      fence_async_smem();
+      tc_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&a_ready[kb]);
+    };
+    auto put_a = [&](int col, const float (&o)[kCc], float inv) {
+      if constexpr (F8) {
+        uint32_t hq[4];
+#pragma unroll
+        for (int i = 0; i < kCc; i += 4)
+          hq[i / 4] = pack_e4m3x4(o[i] * inv, o[i + 1] * inv, o[i + 2] * inv, o[i + 3] * inv);
+        *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
+      } else {
+        uint32_t hp[8];
+#pragma unroll
+        for (int i = 0; i < kCc; i += 2) hp[i / 2] = pack_bf16(o[i], o[i + 1]);
+        *reinterpret_cast<uint4*>(sA + a_off(r, col)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+        *reinterpret_cast<uint4*>(sA + a_off(r, col + 8)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+      }
+    };
+    // silu'(z_q), q = 1, 2, 3, of columns col .. col + 15 into slot q
+    auto put_d = [&](int q, int col, const uint32_t (&dp)[kCc / 2]) {
+      uint8_t* b = sD + (size_t)(q - 1) * C::kD;
+      *reinterpret_cast<uint4*>(b + d_off(r, col)) = make_uint4(dp[0], dp[1], dp[2], dp[3]);
+      *reinterpret_cast<uint4*>(b + d_off(r, col + 8)) = make_uint4(dp[4], dp[5], dp[6], dp[7]);
+    };
     uint32_t acc_phase = 0, red_phase = 0, xph = 0;
     for (int64_t t = 0; t < my_tiles; ++t) {
       const int64_t u0 = (blockIdx.x + t * gridDim.x) * kRows;
@@ -526,25 +573,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
       bool ok = true;
       float sa = 1.f;                                  // FP8: dequantisation scale of this A row
-      // ---- layer 1 in FP32: h1 -> A, silu'(z1) -> TMEM [H, 3H/2)
+      // ---- layer 1 in FP32: h1 -> A, silu'(z1) -> slot 1
       {
         float inv = 1.f;
         if constexpr (F8) {
           float m = 0.2785f;                           // silu(z) >= -0.2785
-          for (int cc = 0; cc < C::kCols; ++cc) {
-            const int col = c0 + cc;
-            float u = pb1[col];
+          for (int j = 0; j < C::kChunks; ++j)
+            for (int i = 0; i < kCc; ++i) {
+              const int col = ccol(j) + i;
+              float u = pb1[col];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) u = fmaf(pW1[c * H + col], x[c], u);
-            m = fmaxf(m, 2.f * u);
-          }
+              for (int c = 0; c < 6; ++c) u = fmaf(pW1[c * H + col], x[c], u);
+              m = fmaxf(m, 2.f * u);
+            }
           const bool got = group_max(m, xch, &xbar[g], xph, cg, r, abort_flag, gerr);
           if (!__all_sync(0xffffffffu, got)) break;
           inv = 448.f / m;
           sa = m / 448.f;
         }
-        for (int cc = 0; cc < C::kCols; cc += kCc) {
-          const int col = c0 + cc;
+#pragma unroll 1
+        for (int j = 0; j < C::kChunks; ++j) {
+          const int col = ccol(j);
           float h[kCc];
           uint32_t dp[kCc / 2];
 #pragma unroll
@@ -560,25 +609,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             f2unpack(dd2, d0, d1);
             dp[i / 2] = pack_bf16(d0, d1);
           }
-          if constexpr (F8) {
-            uint32_t hq[4];
-#pragma unroll
-            for (int i = 0; i < kCc; i += 4)
-              hq[i / 4] = pack_e4m3x4(h[i] * inv, h[i + 1] * inv, h[i + 2] * inv, h[i + 3] * inv);
-            *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
-          } else {
-            uint32_t hp[8];
-#pragma unroll
-            for (int i = 0; i < kCc; i += 2) hp[i / 2] = pack_bf16(h[i], h[i + 1]);
-            *reinterpret_cast<uint4*>(sA + a_off(r, col)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-            *reinterpret_cast<uint4*>(sA + a_off(r, col + 8)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
-          }
-          tmem_st8(lane_addr + H + col / 2, dp);
+          put_a(col, h, inv);
+          put_d(1, col, dp);
+          if ((j + 1) % C::kCpk == 0) a_done(j / C::kCpk);
         }
-        tmem_wait_st();
-        fence_async_smem();
-        tc_before();
-        mbar_arrive(a_ready);
       }
       // ---- hidden layers (forward) and the reverse sweep
       for (int layer = 0; layer < 6; ++layer) {
@@ -586,6 +620,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
         acc_phase ^= 1;
         tc_after();
+        const uint32_t acc = lane_addr + (uint32_t)((layer & 1) * H);   // this product's accumulator
         const float* sw = wsc + layer * H;             // FP8 column scales of this image
         float inv = 1.f, sa_next = sa;
         if constexpr (F8) {
@@ -593,10 +628,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // bound of the row for the next A operand (silu(z) forward, delta backward)
             const float* bias = pb + layer * H;
             float m = layer <= 1 ? 0.2785f : 1e-30f;
-            for (int cc = 0; cc < C::kCols; cc += kCc) {
-              const int col = c0 + cc;
+            for (int j = 0; j < C::kChunks; ++j) {
+              const int col = ccol(j);
               float v[kCc];
-              tmem_ld16f(lane_addr + col, v);
+              tmem_ld16f(acc + col, v);
               tmem_wait_ld();
               if (layer <= 1) {
 #pragma unroll
@@ -615,10 +650,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             sa_next = s4;
           }
         }
-        for (int cc = 0; cc < C::kCols; cc += kCc) {
-          const int col = c0 + cc;
+#pragma unroll 1
+        for (int j = 0; j < C::kChunks; ++j) {
+          const int col = ccol(j);
+          uint32_t dd[kCc / 2];
+          if (layer >= 3) {
+            // silu'(z_{6 - layer}) of these columns, loaded ahead of the accumulator
+            const uint8_t* b = sD + (size_t)(5 - layer) * C::kD;
+            const uint4 w0 = *reinterpret_cast<const uint4*>(b + d_off(r, col));
+            const uint4 w1 = *reinterpret_cast<const uint4*>(b + d_off(r, col + 8));
+            dd[0] = w0.x; dd[1] = w0.y; dd[2] = w0.z; dd[3] = w0.w;
+            dd[4] = w1.x; dd[5] = w1.y; dd[6] = w1.z; dd[7] = w1.w;
+          }
           float v[kCc];
-          tmem_ld16f(lane_addr + col, v);
+          tmem_ld16f(acc + col, v);
           tmem_wait_ld();
           if constexpr (F8) {
 #pragma unroll
@@ -649,24 +694,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 dp[i / 2] = pack_bf16(d0, d1);
               }
             }
-            if (layer == 0) {
-              tmem_st8(lane_addr + H + H / 2 + col / 2, dp);                          // silu'(z2)
-            } else if (layer == 1) {
-              *reinterpret_cast<uint4*>(sD3 + d3_off(r, col)) = make_uint4(dp[0], dp[1], dp[2], dp[3]);
-              *reinterpret_cast<uint4*>(sD3 + d3_off(r, col + 8)) = make_uint4(dp[4], dp[5], dp[6], dp[7]);
-            }
+            if (layer < 2) put_d(layer + 2, col, dp);  // silu'(z2), silu'(z3)
           } else {
             // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
-            uint32_t dd[kCc / 2];
-            if (layer == 3) {
-              const uint4 w0 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col));
-              const uint4 w1 = *reinterpret_cast<const uint4*>(sD3 + d3_off(r, col + 8));
-              dd[0] = w0.x; dd[1] = w0.y; dd[2] = w0.z; dd[3] = w0.w;
-              dd[4] = w1.x; dd[5] = w1.y; dd[6] = w1.z; dd[7] = w1.w;
-            } else {
-              tmem_ld8(lane_addr + H + (layer == 4 ? H / 2 : 0) + col / 2, dd);
-              tmem_wait_ld();
-            }
 #pragma unroll
             for (int i = 0; i < kCc; i += 2)
               f2unpack(f2mul(f2pack(v[i], v[i + 1]), f2pack(bf16_lo(dd[i / 2]), bf16_hi(dd[i / 2]))), o[i],
@@ -690,35 +720,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           }
           if (layer < 5) {
-            if constexpr (F8) {
-              uint32_t hq[4];
-#pragma unroll
-              for (int i = 0; i < kCc; i += 4)
-                hq[i / 4] = pack_e4m3x4(o[i] * inv, o[i + 1] * inv, o[i + 2] * inv, o[i + 3] * inv);
-              *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
-            } else {
-              uint32_t hp[8];
-#pragma unroll
-              for (int i = 0; i < kCc; i += 2) hp[i / 2] = pack_bf16(o[i], o[i + 1]);
-              *reinterpret_cast<uint4*>(sA + a_off(r, col)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-              *reinterpret_cast<uint4*>(sA + a_off(r, col + 8)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
-            }
+            put_a(col, o, inv);
+            if ((j + 1) % C::kCpk == 0) a_done(j / C::kCpk);
           }
         }
+        if (!ok) break;
         sa = sa_next;
-        if (layer == 0) tmem_wait_st();
-        if (layer < 5) {
-          fence_async_smem();
-          tc_before();
-          mbar_arrive(a_ready);
-        }
       }
       if (!ok) break;
       // combine the column groups of each row (fixed order) and write T, dT/dx:
-      // the partial sums go through TMEM columns 3H/2 + [4 cg, 4 cg + 4), next
-      // written by the next tile's layer-2 epilogue (after every thread's
-      // layer-1 arrival)
-      const uint32_t red_addr = lane_addr + (uint32_t)(H + H / 2);
+      // the partial sums go through accumulator columns [4 cg, 4 cg + 4) of
+      // [0, H), last read by the product-4 epilogue and next written by the next
+      // tile's first product (after every warp's layer-1 arrivals)
+      const uint32_t red_addr = lane_addr;
       {
         const uint32_t pr[4] = {__float_as_uint(tpart), __float_as_uint(gpart[0]), __float_as_uint(gpart[1]),
                                 __float_as_uint(gpart[2])};
@@ -867,7 +881,7 @@ cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, 
   return cudaSuccess;
 }
 
-// scratch: num_sms x 128 x H BF16 (the silu'(z3) slots), see tt_scratch_floats
+// scratch: num_sms x 3 x 128 x H BF16 (the silu'(z1..3) slots), see tt_scratch_floats
 cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms, float* scratch,
                           cudaStream_t st) {
   if (!net.tc || !net.err || !scratch) return cudaErrorNotSupported;

@@ -265,7 +265,7 @@ int mlp_fp32_grid(int num_sms) { return 2 * num_sms; }
 size_t tt_scratch_floats(const NetView& net, int num_sms) {
   if (net.kind != SPIDER_TT_MLP) return 0;
   const size_t fp32 = (size_t)mlp_fp32_grid(num_sms) * 3 * net.H * kTP;
-  const size_t tc = (size_t)num_sms * 128 * net.H / 2;     // 128 x H BF16 per SM
+  const size_t tc = (size_t)num_sms * 3 * 128 * net.H / 2; // three 128 x H BF16 slots per SM
   return fp32 > tc ? fp32 : tc;
 }
 

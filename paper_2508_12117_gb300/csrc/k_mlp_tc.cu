@@ -475,7 +475,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = F8 ? idesc_e4m3(H) : idesc_bf16(H);
-      const uint32_t a_base = su32(sA), b_base = su32(sB);
+      // descriptor of address a + d (d a multiple of 16, the sum below 2^18) = desc(a) + d / 16
+      const uint64_t adesc = sw128_desc(su32(sA)), bdesc = sw128_desc(su32(sB));
       int64_t n = 0;        // weight chunks consumed
       uint32_t a_phase = 0;
       bool ok = true;
@@ -490,13 +491,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int s = (int)(n % kStages);
             if (!mbar_wait(&full[s], (uint32_t)((n / kStages) & 1), abort_flag, gerr)) { ok = false; break; }
             tc_after();
+            const uint64_t ad = adesc + (uint64_t)(kb * (kRows * 128 / 16));
+            const uint64_t bd = bdesc + (uint64_t)(s * (C::kChunk / 16));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint64_t ad = sw128_desc(a_base + kb * (kRows * 128) + k * 32);
-              const uint64_t bd = sw128_desc(b_base + s * C::kChunk + k * 32);
-              umma<F8>(d, ad, bd, idesc, (kb | k) ? 1u : 0u);
-              ++issued;
-            }
+            for (int k = 0; k < 4; ++k) umma<F8>(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) ? 1u : 0u);
+            issued += 4;
             umma_commit(&empty[s]);
           }
           if (!ok) break;
@@ -650,17 +649,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             sa_next = s4;
           }
         }
+        // reverse layers: silu'(z_{6 - layer}) of chunk j + 1 is loaded while chunk j
+        // is processed (BF16 with four or more chunks per thread; else chunk by chunk)
+        constexpr bool kAhead = !F8 && C::kChunks >= 4;
+        const uint8_t* dsl = sD + (size_t)(layer >= 3 ? 5 - layer : 0) * C::kD;
+        uint4 dn0 = make_uint4(0, 0, 0, 0), dn1 = dn0;
+        if (kAhead && layer >= 3) {
+          dn0 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(0)));
+          dn1 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(0) + 8));
+        }
 #pragma unroll 1
         for (int j = 0; j < C::kChunks; ++j) {
           const int col = ccol(j);
           uint32_t dd[kCc / 2];
           if (layer >= 3) {
-            // silu'(z_{6 - layer}) of these columns, loaded ahead of the accumulator
-            const uint8_t* b = sD + (size_t)(5 - layer) * C::kD;
-            const uint4 w0 = *reinterpret_cast<const uint4*>(b + d_off(r, col));
-            const uint4 w1 = *reinterpret_cast<const uint4*>(b + d_off(r, col + 8));
-            dd[0] = w0.x; dd[1] = w0.y; dd[2] = w0.z; dd[3] = w0.w;
-            dd[4] = w1.x; dd[5] = w1.y; dd[6] = w1.z; dd[7] = w1.w;
+            if (!kAhead) {
+              dn0 = *reinterpret_cast<const uint4*>(dsl + d_off(r, col));
+              dn1 = *reinterpret_cast<const uint4*>(dsl + d_off(r, col + 8));
+            }
+            dd[0] = dn0.x; dd[1] = dn0.y; dd[2] = dn0.z; dd[3] = dn0.w;
+            dd[4] = dn1.x; dd[5] = dn1.y; dd[6] = dn1.z; dd[7] = dn1.w;
+            if (kAhead && j + 1 < C::kChunks) {
+              dn0 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j + 1)));
+              dn1 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j + 1) + 8));
+            }
           }
           float v[kCc];
           tmem_ld16f(acc + col, v);

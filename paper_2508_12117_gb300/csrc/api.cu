@@ -164,7 +164,7 @@ cudaError_t upload_net(const spider_net* in, int precision, NetView* nv, std::ve
       void* img = nullptr;
       float* sc = nullptr;
       const float* Wn_host[3] = {in->W[1], in->W[2], in->W[3]};
-      if ((e = mlp_tc_prepare(Wn_host, in->W[4], H, precision, &img, &sc, st))) return e;
+      if ((e = mlp_tc_prepare(in->W[0], Wn_host, in->W[4], H, precision, &img, &sc, st))) return e;
       if (img) list.push_back(img);
       if (sc) list.push_back(sc);
       n.tc = img;

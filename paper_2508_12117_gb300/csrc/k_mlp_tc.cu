@@ -1,7 +1,11 @@
 // Tensor-core (tcgen05, sm_103a) form of the travel-time MLP: forward pass and
 // source Jacobian for tiles of 128 (event, station) pairs (Sec. 2.1, Sec. 3.2).
 //
-//   layer 1 (6 -> H, FP32, CUDA cores)  h1 = silu(W1 [x; s] + b1)
+//   layer 1 (6 -> H)  h1 = silu(W1 [x; s] + b1): BF16 form on the tensor cores
+//       with operands split in BF16 pairs, v = v_hi + v_lo: the operand row
+//       [x_hi, x_lo, x_hi, 0 ...] against [W_hi, W_hi, W_lo, 0 ...] (K = 32) gives
+//       W1 [x; s] up to the dropped W_lo x_lo (relative 2^-16 of each term); FP8
+//       form in FP32 on the CUDA cores
 //   layers 2..4 (H x H, BF16 x BF16 or E4M3 x E4M3 -> FP32 in TMEM)  h_l = silu(W_l h_{l-1} + b_l)
 //   output (H -> 1, FP32)  tau = w5 . h4 + b5,  T = |x - s| tau  (double-float outer product)
 //   reverse sweep (H x H, BF16 -> FP32 in TMEM)
@@ -21,7 +25,8 @@
 //              K = 16, A = activations (SW128 K-major, shared memory),
 //              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
 // TMEM (2H columns): two accumulators, [0, H) for products 0, 2, 4 and [H, 2H)
-// for products 1, 3, 5 (forward W2, W3, W4, reverse W4^T, W3^T, W2^T).  Product
+// for products -1 (BF16: the first layer), 1, 3, 5 (forward W2, W3, W4, reverse
+// W4^T, W3^T, W2^T).  Product
 // l + 1 starts on K-block kb of its operand as soon as the epilogue of product l
 // has written that K-block (one barrier per K-block), into the accumulator the
 // epilogue is not reading; only its last K-block is left when the epilogue
@@ -88,7 +93,8 @@ struct Cfg {
   static constexpr int kChunks = kCols / kCc;       // chunks per thread and layer
   static_assert(KB <= kMaxKb && kChunks == KB * kCpk && kCpk >= 1, "tile shape");
   static constexpr int kTmemCols = 2 * H;
-  static constexpr int kChunksPerTile = 6 * KB;
+  static constexpr int kL1 = F8 ? 0 : 1;             // BF16: the first layer's image, one K-block
+  static constexpr int kChunksPerTile = kL1 + 6 * KB;
   // shared-memory carve-up (offsets from a 1024-aligned base)
   static constexpr int oA = 0;
   static constexpr int oB = oA + kA;
@@ -434,8 +440,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int s = (int)(n % kStages);
         const int64_t use = n / kStages;
         if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), abort_flag, gerr)) break;
+        // the images are stored in consumption order, K-block after K-block
         const int c = (int)(n % C::kChunksPerTile);
-        const uint8_t* g = wimg + (size_t)(c / C::KB) * C::kImage + (size_t)(c % C::KB) * C::kChunk;
+        const uint8_t* g = wimg + (size_t)c * C::kChunk;
         mbar_expect_tx(&full[s], C::kChunk);
         bulk_load(sB + s * C::kChunk, g, C::kChunk, &full[s]);
       }
@@ -478,16 +485,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // descriptor of address a + d (d a multiple of 16, the sum below 2^18) = desc(a) + d / 16
       const uint64_t adesc = sw128_desc(su32(sA)), bdesc = sw128_desc(su32(sB));
       int64_t n = 0;        // weight chunks consumed
-      uint32_t a_phase = 0;
+      uint32_t a_phase = 0;  // bit kb: phase of a_ready[kb]
       bool ok = true;
       int issued = 0;
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
+        if constexpr (!F8) {
+          // product -1: the split first layer, K = 32 of K-block 0, into [H, 2H)
+          if (!mbar_wait(&a_ready[0], a_phase & 1u, abort_flag, gerr)) { ok = false; break; }
+          a_phase ^= 1u;
+          const int s = (int)(n % kStages);
+          if (!mbar_wait(&full[s], (uint32_t)((n / kStages) & 1), abort_flag, gerr)) { ok = false; break; }
+          tc_after();
+          const uint64_t bd = bdesc + (uint64_t)(s * (C::kChunk / 16));
+          umma<F8>(tmem + (uint32_t)H, adesc, bd, idesc, 0u);
+          umma<F8>(tmem + (uint32_t)H, adesc + 2, bd + 2, idesc, 1u);
+          issued += 2;
+          umma_commit(&empty[s]);
+          ++n;
+          umma_commit(acc_ready);
+        }
         for (int layer = 0; layer < 6 && ok; ++layer) {
           const uint32_t d = tmem + (uint32_t)((layer & 1) * H);     // this product's accumulator
           for (int kb = 0; kb < C::KB; ++kb, ++n) {
             // K-block kb of the operand written (and the accumulator free: its last
             // reader, the epilogue two products back, finished before)
-            if (!mbar_wait(&a_ready[kb], a_phase, abort_flag, gerr)) { ok = false; break; }
+            if (!mbar_wait(&a_ready[kb], (a_phase >> kb) & 1u, abort_flag, gerr)) { ok = false; break; }
+            a_phase ^= 1u << kb;
             const int s = (int)(n % kStages);
             if (!mbar_wait(&full[s], (uint32_t)((n / kStages) & 1), abort_flag, gerr)) { ok = false; break; }
             tc_after();
@@ -500,7 +523,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           if (!ok) break;
           umma_commit(acc_ready);
-          a_phase ^= 1;
         }
       }
       if (!ok && issued) {
@@ -572,6 +594,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
       bool ok = true;
       float sa = 1.f;                                  // FP8: dequantisation scale of this A row
+      if constexpr (!F8) {
+        // ---- operand of the first layer: [x_hi, x_lo, x_hi, 0 ...], this column
+        // group's 8 of the row's 32 BF16 values in K-block 0
+        float xs[32];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const float hi = __bfloat162float(__float2bfloat16_rn(x[c]));
+          xs[c] = hi;
+          xs[6 + c] = __bfloat162float(__float2bfloat16_rn(x[c] - hi));
+          xs[12 + c] = hi;
+        }
+#pragma unroll
+        for (int k = 18; k < 32; ++k) xs[k] = 0.f;
+        uint32_t q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float a = 0.f, b = 0.f;
+#pragma unroll
+          for (int gq = 0; gq < kGroups; ++gq)
+            if (gq == cg) {
+              a = xs[8 * gq + 2 * i];
+              b = xs[8 * gq + 2 * i + 1];
+            }
+          q[i] = pack_bf16(a, b);
+        }
+        *reinterpret_cast<uint4*>(sA + a_off(r, 8 * cg)) = make_uint4(q[0], q[1], q[2], q[3]);
+        a_done(0);
+      } else {
       // ---- layer 1 in FP32: h1 -> A, silu'(z1) -> slot 1
       {
         float inv = 1.f;
@@ -613,14 +663,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if ((j + 1) % C::kCpk == 0) a_done(j / C::kCpk);
         }
       }
-      // ---- hidden layers (forward) and the reverse sweep
-      for (int layer = 0; layer < 6; ++layer) {
+      }
+      // ---- the first layer (BF16, product -1), hidden layers and the reverse sweep
+      for (int layer = F8 ? 0 : -1; layer < 6; ++layer) {
         const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
         acc_phase ^= 1;
         tc_after();
         const uint32_t acc = lane_addr + (uint32_t)((layer & 1) * H);   // this product's accumulator
-        const float* sw = wsc + layer * H;             // FP8 column scales of this image
+        const float* sw = wsc + (layer > 0 ? layer : 0) * H;   // FP8 column scales of this image
         float inv = 1.f, sa_next = sa;
         if constexpr (F8) {
           if (layer == 0 || layer == 1 || layer == 3 || layer == 4) {
@@ -683,7 +734,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           float o[kCc];                                // next A operand values (unscaled)
           if (layer < 3) {
-            // forward layers 2..4
+            // forward layers 1 (BF16) .. 4; pb - H is b1 / 2
             const float* bias = pb + layer * H;
             uint32_t dp[kCc / 2];
 #pragma unroll
@@ -706,7 +757,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 dp[i / 2] = pack_bf16(d0, d1);
               }
             }
-            if (layer < 2) put_d(layer + 2, col, dp);  // silu'(z2), silu'(z3)
+            if (layer < 2) put_d(layer + 2, col, dp);  // silu'(z1) (BF16), silu'(z2), silu'(z3)
           } else {
             // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
 #pragma unroll
@@ -830,20 +881,43 @@ bool mlp_tc_supported(int H, int precision) {
 // descriptor names.  FP8: every row n of an image is divided by its scale
 // max_k |B[n][k]| / 448 before rounding; `scales` receives the 6 H column
 // scales followed by the scale of delta4, 1.1 max |w5| / 448.
-cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, int H, int precision,
-                           void** image, float** scales, cudaStream_t st) {
+cudaError_t mlp_tc_prepare(const float* W1_host, const float* const Wn_host[3], const float* w5_host, int H,
+                           int precision, void** image, float** scales, cudaStream_t st) {
   *image = nullptr;
   *scales = nullptr;
   if (!mlp_tc_supported(H, precision)) return cudaErrorNotSupported;
   const bool f8 = precision == SPIDER_FP8;
   const int eb = f8 ? 1 : 2, per_kb = 128 / eb;
   const size_t img = (size_t)H * H * eb;
-  std::vector<uint8_t> host(6 * img, 0);
+  // BF16: the first layer's split image (one K-block, H rows x 128 B) in front
+  const size_t pre = f8 ? 0 : (size_t)H * 128;
+  std::vector<uint8_t> host(pre + 6 * img, 0);
   std::vector<float> sc(f8 ? 6 * H + 1 : 0, 1.f);
+  // byte offset of (row n, k) in a K-block-major SW128 image
+  auto sw_off = [H, eb, per_kb](int n, int k) {
+    const int kb = k / per_kb, j = (k % per_kb) / (16 / eb);
+    return (size_t)kb * H * 128 + (size_t)(n / 8) * 1024 + (size_t)(n % 8) * 128 + (size_t)((j ^ (n % 8)) * 16) +
+           (size_t)(k % (16 / eb)) * eb;
+  };
+  if (!f8) {
+    // B[n][k]: W_hi (k < 6), W_hi (6 <= k < 12), W_lo (12 <= k < 18), 0 above
+    for (int n = 0; n < H; ++n)
+      for (int c = 0; c < 6; ++c) {
+        const float w = W1_host[(size_t)n * 6 + c];
+        const uint16_t hi = to_bf16(w);
+        float whi;
+        const uint32_t hb = (uint32_t)hi << 16;
+        std::memcpy(&whi, &hb, 4);
+        const uint16_t lo = to_bf16(w - whi);
+        std::memcpy(host.data() + sw_off(n, c), &hi, 2);
+        std::memcpy(host.data() + sw_off(n, 6 + c), &hi, 2);
+        std::memcpy(host.data() + sw_off(n, 12 + c), &lo, 2);
+      }
+  }
   for (int l = 0; l < 6; ++l) {
     const float* W = Wn_host[l < 3 ? l : 5 - l];
     const bool transpose = l >= 3;
-    uint8_t* base = host.data() + l * img;
+    uint8_t* base = host.data() + pre + l * img;
     for (int n = 0; n < H; ++n) {
       float inv = 1.f;
       if (f8) {
@@ -855,9 +929,7 @@ cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, 
       }
       for (int k = 0; k < H; ++k) {
         const float v = transpose ? W[(size_t)k * H + n] : W[(size_t)n * H + k];
-        const int kb = k / per_kb, j = (k % per_kb) / (16 / eb);
-        const size_t off = (size_t)kb * H * 128 + (size_t)(n / 8) * 1024 + (size_t)(n % 8) * 128 +
-                           (size_t)((j ^ (n % 8)) * 16) + (size_t)(k % (16 / eb)) * eb;
+        const size_t off = sw_off(n, k);
         if (f8) {
           base[off] = to_e4m3(v * inv);
         } else {

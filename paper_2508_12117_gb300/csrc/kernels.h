@@ -18,9 +18,10 @@ cudaError_t launch_tt(const NetView& net, const PairSource& src, TTOut out, int 
 cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms,
                           float* scratch, cudaStream_t st);
 bool mlp_tc_supported(int H, int precision);
-// builds the tensor-core operand images of the hidden layers on the device
-cudaError_t mlp_tc_prepare(const float* const Wn_host[3], const float* w5_host, int H, int precision,
-                           void** image, float** scales, cudaStream_t st);
+// builds the tensor-core operand images (BF16: the first layer's split image,
+// then the hidden layers) on the device
+cudaError_t mlp_tc_prepare(const float* W1_host, const float* const Wn_host[3], const float* w5_host, int H,
+                           int precision, void** image, float** scales, cudaStream_t st);
 
 // step (k_step.cu)
 cudaError_t configure_step_kernels(const StepView& v);

@@ -91,3 +91,40 @@ def test_bf16_round_to_nearest_even(q):
             assert got == hi
         else:
             assert (np.array([got], np.float32).view(np.uint32)[0] >> 16) & 1 == 0
+
+
+def _bf16_value(q, v):
+    b = int(q.quant_bf16(float(v)))
+    return float(np.frombuffer(np.array([b << 16], np.uint32).tobytes(), np.float32)[0])
+
+
+def test_bf16_split_first_layer_bound(q):
+    """The BF16 tensor-core form's first layer: each FP32 operand v is split into
+    BF16 values v_hi = bf16(v), v_lo = bf16(v - v_hi), and the K = 18 product
+    [x_hi, x_lo, x_hi] . [W_hi, W_hi, W_lo] stands for W1 x.  With round to
+    nearest, |v - v_hi - v_lo| <= 2^-18 |v| and the dropped x_lo W_lo is at most
+    2^-18 |x W|, so every term is within 3 * 2^-18 < 2^-15 of x W (products of
+    BF16 values are exact in FP32).  Checked on the network inputs of the
+    synthetic catalogs (coordinates in km) and the seeded first-layer weights."""
+    from paper_2508_12117_gb300 import synth
+    net = synth.mlp_weights(256, 811)
+    W = net["W"][0]                                      # (H, 6), FP32
+    rng = np.random.default_rng(5)
+    n = 400
+    src = np.c_[rng.uniform(0, 60, n), rng.uniform(0, 60, n), rng.uniform(2, 16, n)]
+    rcv = np.c_[rng.uniform(-10, 70, n), rng.uniform(-10, 70, n), np.zeros(n)]
+    x = np.c_[src, rcv].astype(np.float32)
+
+    def split(a):
+        hi = np.vectorize(lambda v: _bf16_value(q, v))(a).astype(np.float32)
+        lo = np.vectorize(lambda v: _bf16_value(q, v))((a - hi).astype(np.float32)).astype(np.float32)
+        return hi.astype(np.float64), lo.astype(np.float64)
+
+    xh, xl = split(x)
+    wh, wl = split(W)
+    exact = x.astype(np.float64) @ W.T.astype(np.float64)
+    approx = xh @ wh.T + xl @ wh.T + xh @ wl.T
+    scale = np.abs(x.astype(np.float64)) @ np.abs(W.T.astype(np.float64))
+    assert np.all(np.abs(approx - exact) <= 2.0 ** -15 * scale)
+    # and a plain BF16 product (no split) would not meet it
+    assert np.max(np.abs(xh @ wh.T - exact) / scale) > 2.0 ** -12

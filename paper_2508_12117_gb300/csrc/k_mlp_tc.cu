@@ -1,11 +1,10 @@
 // Tensor-core (tcgen05, sm_103a) form of the travel-time MLP: forward pass and
 // source Jacobian for tiles of 128 (event, station) pairs (Sec. 2.1, Sec. 3.2).
 //
-//   layer 1 (6 -> H)  h1 = silu(W1 [x; s] + b1): BF16 form on the tensor cores
+//   layer 1 (6 -> H)  h1 = silu(W1 [x; s] + b1): a BF16 product in both forms,
 //       with operands split in BF16 pairs, v = v_hi + v_lo: the operand row
 //       [x_hi, x_lo, x_hi, 0 ...] against [W_hi, W_hi, W_lo, 0 ...] (K = 32) gives
-//       W1 [x; s] up to the dropped W_lo x_lo (relative 2^-16 of each term); FP8
-//       form in FP32 on the CUDA cores
+//       W1 [x; s] up to the dropped W_lo x_lo (relative 2^-16 of each term)
 //   layers 2..4 (H x H, BF16 x BF16 or E4M3 x E4M3 -> FP32 in TMEM)  h_l = silu(W_l h_{l-1} + b_l)
 //   output (H -> 1, FP32)  tau = w5 . h4 + b5,  T = |x - s| tau  (double-float outer product)
 //   reverse sweep (H x H, BF16 -> FP32 in TMEM)
@@ -25,7 +24,7 @@
 //              K = 16, A = activations (SW128 K-major, shared memory),
 //              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
 // TMEM (2H columns): two accumulators, [0, H) for products 0, 2, 4 and [H, 2H)
-// for products -1 (BF16: the first layer), 1, 3, 5 (forward W2, W3, W4, reverse
+// for products -1 (the first layer), 1, 3, 5 (forward W2, W3, W4, reverse
 // W4^T, W3^T, W2^T).  Product
 // l + 1 starts on K-block kb of its operand as soon as the epilogue of product l
 // has written that K-block (one barrier per K-block), into the accumulator the
@@ -92,8 +91,7 @@ struct Cfg {
   static constexpr int kChunks = kCols / kCc;       // chunks per thread and layer
   static_assert(KB <= kMaxKb && kChunks == KB * kCpk && kCpk >= 1, "tile shape");
   static constexpr int kTmemCols = 2 * H;
-  static constexpr int kL1 = F8 ? 0 : 1;             // BF16: the first layer's image, one K-block
-  static constexpr int kChunksPerTile = kL1 + 6 * KB;
+  static constexpr int kChunksPerTile = 1 + 6 * KB;  // the first layer's image (one K-block), then 6 layers
   // shared-memory carve-up (offsets from a 1024-aligned base)
   static constexpr int oA = 0;
   static constexpr int oB = oA + kA;
@@ -439,16 +437,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       bool ok = true;
       int issued = 0;
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
-        if constexpr (!F8) {
-          // product -1: the split first layer, K = 32 of K-block 0, into [H, 2H)
+        {
+          // product -1: the split first layer (BF16 in both forms), K = 32 of
+          // K-block 0, into [H, 2H)
           if (!mbar_wait(&a_ready[0], a_phase & 1u, abort_flag, gerr)) { ok = false; break; }
           a_phase ^= 1u;
           const int s = (int)(n % kStages);
           if (!mbar_wait(&full[s], (uint32_t)((n / kStages) & 1), abort_flag, gerr)) { ok = false; break; }
           tc_after();
+          constexpr uint32_t idesc1 = idesc_bf16(H);
           const uint64_t bd = bdesc + (uint64_t)(s * (C::kChunk / 16));
-          umma<F8>(tmem + (uint32_t)H, adesc, bd, idesc, 0u);
-          umma<F8>(tmem + (uint32_t)H, adesc + 2, bd + 2, idesc, 1u);
+          umma<false>(tmem + (uint32_t)H, adesc, bd, idesc1, 0u);
+          umma<false>(tmem + (uint32_t)H, adesc + 2, bd + 2, idesc1, 1u);
           issued += 2;
           umma_commit(&empty[s]);
           ++n;
@@ -538,15 +538,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         x[c] = gb[c * kRows + r] + (gb[(3 + c) * kRows + r] + gb[(6 + c) * kRows + r]);
         x[3 + c] = gb[(9 + c) * kRows + r] + gb[(12 + c) * kRows + r];
       }
-      uint64_t x2[6];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) x2[c] = f2pack(x[c], x[c]);
       float tpart = 0.f, gpart[3] = {0.f, 0.f, 0.f};
       bool ok = true;
       float sa = 1.f;                                  // FP8: dequantisation scale of this A row
-      if constexpr (!F8) {
+      {
         // ---- operand of the first layer: [x_hi, x_lo, x_hi, 0 ...], this column
-        // group's 8 of the row's 32 BF16 values in K-block 0
+        // group's 8 of the row's 32 BF16 values in K-block 0 (BF16 in both forms)
         float xs[32];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -571,60 +568,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         *reinterpret_cast<uint4*>(sA + a_off(r, 8 * cg)) = make_uint4(q[0], q[1], q[2], q[3]);
         a_done(0);
-      } else {
-      // ---- layer 1 in FP32: h1 -> A, silu'(z1) -> slot 1
-      {
-        float inv = 1.f;
-        if constexpr (F8) {
-          float m = 0.2785f;                           // silu(z) >= -0.2785
-          for (int j = 0; j < C::kChunks; ++j)
-            for (int i = 0; i < kCc; ++i) {
-              const int col = ccol(j) + i;
-              float u = pb1[col];
-#pragma unroll
-              for (int c = 0; c < 6; ++c) u = fmaf(pW1[c * H + col], x[c], u);
-              m = fmaxf(m, 2.f * u);
-            }
-          const bool got = group_max(m, xch, &xbar[g], xph, cg, r, abort_flag, gerr);
-          if (!__all_sync(0xffffffffu, got)) break;
-          inv = 448.f / m;
-          sa = m / 448.f;
-        }
-#pragma unroll 1
-        for (int j = 0; j < C::kChunks; ++j) {
-          const int col = ccol(j);
-          float h[kCc];
-          uint32_t dp[kCc / 2];
-#pragma unroll
-          for (int i = 0; i < kCc; i += 2) {
-            uint64_t u = *reinterpret_cast<const uint64_t*>(pb1 + col + i);
-#pragma unroll
-            for (int c = 0; c < 6; ++c)
-              u = f2fma(*reinterpret_cast<const uint64_t*>(pW1 + c * H + col + i), x2[c], u);
-            uint64_t hh, dd2;
-            silu_half(u, hh, dd2);
-            float d0, d1;
-            f2unpack(hh, h[i], h[i + 1]);
-            f2unpack(dd2, d0, d1);
-            dp[i / 2] = pack_bf16(d0, d1);
-          }
-          put_a(col, h, inv);
-          put_d(1, col, dp);
-          if ((j + 1) % C::kCpk == 0) a_done(j / C::kCpk);
-        }
       }
-      }
-      // ---- the first layer (BF16, product -1), hidden layers and the reverse sweep
-      for (int layer = F8 ? 0 : -1; layer < 6; ++layer) {
+      // ---- the first layer (product -1), hidden layers and the reverse sweep
+      for (int layer = -1; layer < 6; ++layer) {
         const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
         acc_phase ^= 1;
         tc_after();
         const uint32_t acc = lane_addr + (uint32_t)((layer & 1) * H);   // this product's accumulator
-        const float* sw = wsc + (layer > 0 ? layer : 0) * H;   // FP8 column scales of this image
+        // FP8: dequantisation of the accumulator, (row scale) x (column scale); the
+        // first layer's BF16 product needs none
+        const float* sw = wsc + (layer > 0 ? layer : 0) * H;
+        const float sa_l = layer < 0 ? 0.f : sa;
+        auto dq = [&](int c) { return layer < 0 ? 1.f : sa_l * sw[c]; };
         float inv = 1.f, sa_next = sa;
         if constexpr (F8) {
-          if (layer == 0 || layer == 1 || layer == 3 || layer == 4) {
+          if (layer == -1 || layer == 0 || layer == 1 || layer == 3 || layer == 4) {
             // bound of the row for the next A operand (silu(z) forward, delta backward)
             const float* bias = pb + layer * H;
             float m = layer <= 1 ? 0.2785f : 1e-30f;
@@ -635,10 +594,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               tmem_wait_ld();
               if (layer <= 1) {
 #pragma unroll
-                for (int i = 0; i < kCc; ++i) m = fmaxf(m, 2.f * fmaf(v[i] * (sa * sw[col + i]), 0.5f, bias[col + i]));
+                for (int i = 0; i < kCc; ++i) m = fmaxf(m, 2.f * fmaf(v[i] * dq(col + i), 0.5f, bias[col + i]));
               } else {
 #pragma unroll
-                for (int i = 0; i < kCc; ++i) m = fmaxf(m, 1.1f * fabsf(v[i] * (sa * sw[col + i])));
+                for (int i = 0; i < kCc; ++i) m = fmaxf(m, 1.1f * fabsf(v[i] * dq(col + i)));
               }
             }
             const bool got2 = group_max(m, xch, &xbar[g], xph, cg, r, abort_flag, gerr);
@@ -680,11 +639,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tmem_wait_ld();
           if constexpr (F8) {
 #pragma unroll
-            for (int i = 0; i < kCc; ++i) v[i] *= sa * sw[col + i];
+            for (int i = 0; i < kCc; ++i) v[i] *= dq(col + i);
           }
           float o[kCc];                                // next A operand values (unscaled)
           if (layer < 3) {
-            // forward layers 1 (BF16) .. 4; pb - H is b1 / 2
+            // forward layers 1 .. 4; pb - H is b1 / 2
             const float* bias = pb + layer * H;
             uint32_t dp[kCc / 2];
 #pragma unroll
@@ -707,7 +666,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 dp[i / 2] = pack_bf16(d0, d1);
               }
             }
-            if (layer < 2) put_d(layer + 2, col, dp);  // silu'(z1) (BF16), silu'(z2), silu'(z3)
+            if (layer < 2) put_d(layer + 2, col, dp);  // silu'(z1), silu'(z2), silu'(z3)
           } else {
             // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
 #pragma unroll
@@ -837,20 +796,22 @@ cudaError_t mlp_tc_prepare(const float* W1_host, const float* const Wn_host[3], 
   *scales = nullptr;
   if (!mlp_tc_supported(H, precision)) return cudaErrorNotSupported;
   const bool f8 = precision == SPIDER_FP8;
-  const int eb = f8 ? 1 : 2, per_kb = 128 / eb;
+  const int eb = f8 ? 1 : 2;
   const size_t img = (size_t)H * H * eb;
-  // BF16: the first layer's split image (one K-block, H rows x 128 B) in front
-  const size_t pre = f8 ? 0 : (size_t)H * 128;
+  // the first layer's split BF16 image (one K-block, H rows x 128 B) in front
+  const size_t pre = (size_t)H * 128;
   std::vector<uint8_t> host(pre + 6 * img, 0);
   std::vector<float> sc(f8 ? 6 * H + 1 : 0, 1.f);
-  // byte offset of (row n, k) in a K-block-major SW128 image
-  auto sw_off = [H, eb, per_kb](int n, int k) {
-    const int kb = k / per_kb, j = (k % per_kb) / (16 / eb);
+  // byte offset of (row n, k) in a K-block-major SW128 image of e-byte elements
+  auto sw_off_e = [H](int n, int k, int e) {
+    const int per = 128 / e, kb = k / per, j = (k % per) / (16 / e);
     return (size_t)kb * H * 128 + (size_t)(n / 8) * 1024 + (size_t)(n % 8) * 128 + (size_t)((j ^ (n % 8)) * 16) +
-           (size_t)(k % (16 / eb)) * eb;
+           (size_t)(k % (16 / e)) * e;
   };
-  if (!f8) {
-    // B[n][k]: W_hi (k < 6), W_hi (6 <= k < 12), W_lo (12 <= k < 18), 0 above
+  auto sw_off = [&](int n, int k) { return sw_off_e(n, k, eb); };
+  {
+    // B[n][k]: W_hi (k < 6), W_hi (6 <= k < 12), W_lo (12 <= k < 18), 0 above,
+    // BF16 in both forms (2-byte elements, K-blocks of 64)
     for (int n = 0; n < H; ++n)
       for (int c = 0; c < 6; ++c) {
         const float w = W1_host[(size_t)n * 6 + c];
@@ -859,9 +820,9 @@ cudaError_t mlp_tc_prepare(const float* W1_host, const float* const Wn_host[3], 
         const uint32_t hb = (uint32_t)hi << 16;
         std::memcpy(&whi, &hb, 4);
         const uint16_t lo = to_bf16(w - whi);
-        std::memcpy(host.data() + sw_off(n, c), &hi, 2);
-        std::memcpy(host.data() + sw_off(n, 6 + c), &hi, 2);
-        std::memcpy(host.data() + sw_off(n, 12 + c), &lo, 2);
+        std::memcpy(host.data() + sw_off_e(n, c, 2), &hi, 2);
+        std::memcpy(host.data() + sw_off_e(n, 6 + c, 2), &hi, 2);
+        std::memcpy(host.data() + sw_off_e(n, 12 + c, 2), &lo, 2);
       }
   }
   for (int l = 0; l < 6; ++l) {

@@ -340,6 +340,40 @@ def test_origin_time_shift_invariance():
     assert abs(like_t0.sum()) < 1e-9 * np.abs(like_t0).sum()
 
 
+def _moved_problem(P, shift=np.zeros(3), phi=0.0):
+    """The same catalog with every event, prior mean and station moved rigidly:
+    rotated by phi about the vertical axis, then shifted."""
+    c, s_ = math.cos(phi), math.sin(phi)
+    R = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+    init = P.init.copy()
+    init[:, :3] = P.init[:, :3] @ R.T + shift
+    sta = P.stations @ R.T + shift
+    return O.Problem(init, sta, P.i, P.j, P.k, P.dt, P.model, P.sigma, P.kappa, P.p, P.ell,
+                     P.eps_w, P.sig_e, P.sig_c, P.batch_n, P.block_obs, P.reorder), R
+
+
+def test_rigid_motion_invariance_homogeneous():
+    # Homogeneous travel times depend on |x - s| only, the edge weights on
+    # inter-event distances, and the priors on theta - theta_0 with equal x and y
+    # widths: moving events, prior means and stations together rigidly leaves the
+    # log posterior unchanged and turns the position gradient with the motion
+    # (a swapped or mis-signed coordinate anywhere breaks this).
+    P = tiny_problem(M=10, S=4, K=4, seed=21)
+    rng = np.random.default_rng(21)
+    d = np.c_[rng.normal(0, 0.2, (P.M, 3)), rng.normal(0, 0.05, P.M)]
+    theta = P.init + d
+    lp, g, _ = O.log_posterior(P, theta)
+    for shift, phi in [(np.array([7.5, -3.25, 1.5]), 0.0), (np.zeros(3), 0.7), (np.array([-2.0, 4.0, 0.5]), -1.9)]:
+        Q, R = _moved_problem(P, shift, phi)
+        th = Q.init.copy()
+        th[:, :3] += d[:, :3] @ R.T
+        th[:, 3] += d[:, 3]
+        lq, gq, _ = O.log_posterior(Q, th)
+        assert abs(lq - lp) <= 1e-9 * abs(lp)
+        assert np.allclose(gq[:, :3], g[:, :3] @ R.T, rtol=1e-8, atol=1e-8 * np.abs(g).max())
+        assert np.allclose(gq[:, 3], g[:, 3], rtol=1e-8, atol=1e-8 * np.abs(g).max())
+
+
 def test_centroid_prior_gradient_is_uniform():
     P = tiny_problem(M=8, S=2, K=3, seed=9)
     theta = P.init + 0.3        # pure translation: the event prior and the centroid pull back

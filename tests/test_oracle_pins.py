@@ -352,18 +352,26 @@ def _moved_problem(P, shift=np.zeros(3), phi=0.0):
                      P.eps_w, P.sig_e, P.sig_c, P.batch_n, P.block_obs, P.reorder), R
 
 
-def test_rigid_motion_invariance_homogeneous():
-    # Homogeneous travel times depend on |x - s| only, the edge weights on
+@pytest.mark.parametrize("kind", ["homogeneous", "gradient"])
+def test_rigid_motion_invariance(kind):
+    # Homogeneous travel times depend on |x - s| only, linear-gradient ones on the
+    # horizontal offset and the two depths; the edge weights depend on
     # inter-event distances, and the priors on theta - theta_0 with equal x and y
-    # widths: moving events, prior means and stations together rigidly leaves the
-    # log posterior unchanged and turns the position gradient with the motion
-    # (a swapped or mis-signed coordinate anywhere breaks this).
-    P = tiny_problem(M=10, S=4, K=4, seed=21)
+    # widths.  Moving events, prior means and stations together rigidly (any
+    # shift for the homogeneous model, horizontal ones for the gradient model,
+    # rotations about the vertical for both) leaves the log posterior unchanged
+    # and turns the position gradient with the motion (a swapped or mis-signed
+    # horizontal coordinate anywhere breaks this).
+    model = {"homogeneous": O.Model("homogeneous", v0=6.0),
+             "gradient": O.Model("gradient", v0=5.0, g=0.05)}[kind]
+    P = tiny_problem(M=10, S=4, K=4, seed=21, model=model)
     rng = np.random.default_rng(21)
     d = np.c_[rng.normal(0, 0.2, (P.M, 3)), rng.normal(0, 0.05, P.M)]
     theta = P.init + d
     lp, g, _ = O.log_posterior(P, theta)
-    for shift, phi in [(np.array([7.5, -3.25, 1.5]), 0.0), (np.zeros(3), 0.7), (np.array([-2.0, 4.0, 0.5]), -1.9)]:
+    dz = 1.0 if kind == "homogeneous" else 0.0
+    for shift, phi in [(np.array([7.5, -3.25, 1.5 * dz]), 0.0), (np.zeros(3), 0.7),
+                       (np.array([-2.0, 4.0, 0.5 * dz]), -1.9)]:
         Q, R = _moved_problem(P, shift, phi)
         th = Q.init.copy()
         th[:, :3] += d[:, :3] @ R.T

@@ -57,8 +57,12 @@ enum {
                                     (the EikoNet stand-in of Sec. 3.2) */
 };
 
-/* arithmetic of the MLP hidden layers (layer 1, output layer, T, residuals
- * and positions are FP32 in every mode) */
+/* arithmetic of the MLP hidden layers.  The output layer, T, residuals and
+ * positions are FP32 in every mode.  Layer 1 is FP32 in SPIDER_FP32; in
+ * SPIDER_BF16 and SPIDER_FP8 it is a tensor-core product of BF16 operand pairs
+ * (v = v_hi + v_lo for the inputs and W1), FP32-accumulated, whose only dropped
+ * term is W1_lo x_lo (at most 2^-16 of each product), followed by FP32 bias and
+ * SiLU. */
 enum { SPIDER_FP32 = 0, SPIDER_BF16 = 1, SPIDER_FP8 = 2 };
 
 typedef struct {

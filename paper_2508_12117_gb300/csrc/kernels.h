@@ -18,7 +18,7 @@ cudaError_t launch_tt(const NetView& net, const PairSource& src, TTOut out, int 
 cudaError_t launch_mlp_tc(const NetView& net, const PairSource& src, TTOut out, int num_sms,
                           float* scratch, cudaStream_t st);
 bool mlp_tc_supported(int H, int precision);
-// builds the tensor-core operand images (BF16: the first layer's split image,
+// builds the tensor-core operand images (the first layer's split BF16 image,
 // then the hidden layers) on the device
 cudaError_t mlp_tc_prepare(const float* W1_host, const float* const Wn_host[3], const float* w5_host, int H,
                            int precision, void** image, float** scales, cudaStream_t st);

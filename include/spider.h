@@ -314,8 +314,11 @@ int spider_tt_pairs(const spider_netdev *nd, int64_t P, const float *src, const 
  * into a process whose allocator must not be touched.  It calls no cudaMalloc,
  * cudaFree or other allocating routine; the caller still passes every input
  * and output (src, rcv, T_hi, T_lo, J as in spider_tt_pairs, all device
- * pointers) and the network as host arrays (net->W, net->b, read during the
- * call).  What the kernel needs besides them -- the weights in the layouts it
+ * pointers) and the network as host arrays (net->W, net->b, checked for
+ * finite values during the call and copied to the device by copies queued on
+ * `stream`: pageable host arrays may be reused once the call returns,
+ * page-locked ones must stay unchanged until the stream has passed the call).
+ * What the kernel needs besides them -- the weights in the layouts it
  * reads, per-CTA slots for silu'(z) between the forward and the reverse sweep,
  * and the (hi, lo) staging of T -- lives in one fixed-size array of static
  * device memory (about 40 MB), which every GPU that loads this library holds
@@ -323,8 +326,9 @@ int spider_tt_pairs(const spider_netdev *nd, int64_t P, const float *src, const 
  * H in {32, 64, 128, 256}, 0 <= P <= 2^20; anything else returns
  * SPIDER_E_UNSUPPORTED or SPIDER_E_INVAL and spider_last_error(NULL) names the
  * limit.  The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's
+ * (once per device, with that device current) and keeps it; make that first
+ * call before any stream capture, and do not call cudaDeviceReset while the
+ * library is loaded.  All calls share the array and it keeps the last call's
  * contents; the kernel writes every word it reads within the same call, so
  * nothing needs clearing, but calls that overlap on the GPU (other streams,
  * other host threads) race on it and must be serialised by the caller.

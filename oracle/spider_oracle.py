@@ -252,15 +252,14 @@ def _silu(z):
     return z * s, s * (1.0 + z * (1.0 - s))
 
 
-def tt_mlp(src, rcv, net: dict):
-    """T = |x - s| * tau(x, s), tau = MLP([x; s]) with SiLU hidden layers.
+def mlp_tau(src, rcv, net: dict):
+    """tau = MLP([x; s]) with SiLU hidden layers and its source gradient dtau/dx.
 
-    Forward in float64 with the given (float32) weights; the source Jacobian
-    by the reverse-mode chain (Sec. 3.2 computes gradients with reverse-mode
+    Forward in float64 with the given (float32) weights; the gradient by the
+    reverse-mode chain (Sec. 3.2 computes gradients with reverse-mode
     automatic differentiation):
       delta_L = W_out^T * silu'(z_L),  delta_{l-1} = (W_l^T delta_l) * silu'(z_{l-1}),
-      dtau/dx = (W_1^T delta_1)[source part],
-      dT/dx = tau (x - s)/r + r dtau/dx."""
+      dtau/dx = (W_1^T delta_1)[source part]."""
     W = [np.asarray(w, dtype=np.float64) for w in net["W"]]
     b = [np.asarray(v, dtype=np.float64) for v in net["b"]]
     x = np.concatenate([src, rcv], -1)
@@ -275,6 +274,13 @@ def tt_mlp(src, rcv, net: dict):
     for l in range(len(W) - 2, 0, -1):
         delta = (delta @ W[l]) * dsil[l - 1]
     dtau = (delta @ W[0])[..., :3]
+    return tau, dtau
+
+
+def tt_mlp(src, rcv, net: dict):
+    """T = |x - s| * tau(x, s), tau = MLP([x; s]) (see `mlp_tau`), and
+    dT/dx = tau (x - s)/r + r dtau/dx."""
+    tau, dtau = mlp_tau(src, rcv, net)
     d = src - rcv
     r = np.sqrt((d * d).sum(-1))
     T = r * tau
@@ -611,6 +617,17 @@ def uq_stats(samples, truth=None, lo_pct=0.5, hi_pct=99.5):
     n, M, _ = s.shape
     ess = np.array([[ess_series(s[:, m, a]) for a in range(4)] for m in range(M)])
     return med, half, calib, ess
+
+
+def grad_noise_ratio(g, G, eps) -> float:
+    """Variance of the stochastic gradient relative to the injected Langevin
+    noise (Sec. 3.6, the quantity the step size is tuned against, 0.1-1): the
+    update's stochastic part eps (g - G) against the noise sqrt(2 eps) eta,
+    eps^2 mean((g - G)^2) / (2 eps), the mean over every event coordinate;
+    g is a minibatch gradient and G the full-batch gradient at the same state.
+    Linear in eps, as the paper notes."""
+    d = np.asarray(g, dtype=np.float64) - np.asarray(G, dtype=np.float64)
+    return float(eps * eps * np.mean(d * d) / (2.0 * eps))
 
 
 def grad_norms(grad) -> np.ndarray:

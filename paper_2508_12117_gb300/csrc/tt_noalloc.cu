@@ -8,6 +8,7 @@
 // exists on every GPU that loads the library, from module load until exit.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "kernels.h"
@@ -33,6 +34,8 @@ float* g_na_ptr[kNaMaxDevices] = {};
 std::mutex g_na_mu;
 
 // device address of the scratch array on the current device, looked up once
+// per device and kept for the life of the process (a cudaDeviceReset while the
+// library is loaded would leave it stale: not supported)
 cudaError_t scratch_address(float** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -79,11 +82,28 @@ extern "C" int spider_tt_pairs_noalloc(const spider_net* net, int64_t P, const f
     na_error("spider_tt_pairs_noalloc: P must be in [0, 2^20]");
     return SPIDER_E_INVAL;
   }
-  for (int l = 0; l < 5; ++l)
-    if (!net->W[l] || !net->b[l]) {
-      na_error("spider_tt_pairs_noalloc: null weight or bias");
-      return SPIDER_E_INVAL;
+  {
+    const size_t wn[5] = {(size_t)H * 6, (size_t)H * H, (size_t)H * H, (size_t)H * H, (size_t)H};
+    const size_t bn[5] = {(size_t)H, (size_t)H, (size_t)H, (size_t)H, 1};
+    for (int l = 0; l < 5; ++l) {
+      if (!net->W[l] || !net->b[l]) {
+        na_error("spider_tt_pairs_noalloc: null weight or bias");
+        return SPIDER_E_INVAL;
+      }
+      // the same rejection as spider_tt_pairs: a NaN or Inf weight would only
+      // surface as NaN travel times
+      for (size_t i = 0; i < wn[l]; ++i)
+        if (!std::isfinite(net->W[l][i])) {
+          na_error("spider_tt_pairs_noalloc: non-finite MLP weight");
+          return SPIDER_E_INVAL;
+        }
+      for (size_t i = 0; i < bn[l]; ++i)
+        if (!std::isfinite(net->b[l][i])) {
+          na_error("spider_tt_pairs_noalloc: non-finite MLP bias");
+          return SPIDER_E_INVAL;
+        }
     }
+  }
   if (P == 0) return SPIDER_OK;
   if (!src || !rcv || !T_hi) {
     na_error("spider_tt_pairs_noalloc: null src, rcv or T_hi");

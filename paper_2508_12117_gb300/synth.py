@@ -284,6 +284,29 @@ def mlp_weights(hidden: int, seed: int) -> dict:
     return {"H": hidden, "W": W, "b": b}
 
 
+def strong_mlp_weights(hidden: int, seed: int, first_scale: float = 1.0 / 20.0) -> dict:
+    """A travel-time network whose learned part is a large share of tau.
+
+    Same shapes and biases as `mlp_weights`, but the hidden and output layers
+    are Xavier-uniform at full scale and the first layer is Xavier-uniform x
+    `first_scale` (the inputs are coordinates in km spanning tens of km, so
+    1/20 keeps the first pre-activations of order one).  Over a 60 x 60 km
+    region tau then varies by about 50 % (roughly 0.18 to 0.27 s/km) and
+    r dtau/dx is about a fifth of dT/dx by rel-L2, so an error anywhere in the
+    reverse sweep shows in the Jacobian and in the gradient.  first_scale = 1
+    gives a network whose output dominates tau entirely."""
+    rng = np.random.default_rng(seed)
+    dims = [6, hidden, hidden, hidden, hidden, 1]
+    W, b = [], []
+    for l in range(5):
+        fi, fo = dims[l], dims[l + 1]
+        bound = math.sqrt(6.0 / (fi + fo)) * (first_scale if l == 0 else 1.0)
+        W.append(rng.uniform(-bound, bound, size=(fo, fi)).astype(np.float32))
+        b.append(np.zeros(fo, dtype=np.float32))
+    b[4][0] = np.float32(1.0 / 5.5)
+    return {"H": hidden, "W": W, "b": b}
+
+
 def make_catalog(s, chunk: int = 1 << 24) -> Catalog:
     """Draw one catalog.  `s` is a workload id or a `Spec`."""
     if isinstance(s, int):

@@ -404,6 +404,74 @@ def test_minibatch_scaling_is_unbiased_when_iid():
     assert np.allclose(acc / nb, gfull, rtol=1e-10, atol=1e-10 * np.abs(gfull).max())
 
 
+def _iid_loss(P, theta, sel):
+    """-1/2 sum r^2 / sigma^2 over the observations sel (the kappa = 0 data term,
+    unscaled), evaluated from the residuals alone."""
+    r, _ = O.residuals(P, theta, sel)
+    return -0.5 * float(r @ r) / P.sigma ** 2
+
+
+def test_grad_noise_ratio_zero_for_the_full_batch():
+    P = tiny_problem(M=10, S=3, K=4, seed=12)
+    theta = P.init + 0.04
+    _, G, _ = O.log_posterior(P, theta)
+    _, g, _ = O.log_posterior(P, theta, np.arange(P.N))     # a "minibatch" of every observation
+    assert O.grad_noise_ratio(g, G, 1e-3) == 0.0
+
+
+def test_grad_noise_ratio_two_block_iid_closed_form():
+    # kappa = 0, two blocks, minibatch = one block: the scaled minibatch
+    # gradient is prior + 2 l_b and the full one prior + l_1 + l_2, so for
+    # either block g - G = +-(l_1 - l_2) and the ratio is eps/2 mean((l_1 - l_2)^2),
+    # with l_b the data-term gradient of block b alone (here by central
+    # differences of the iid loss, independently of the oracle's scatter)
+    P = tiny_problem(M=8, S=3, K=3, seed=13, kappa=0.0)
+    assert P.N % 2 == 0
+    half = P.N // 2
+    P = tiny_problem(M=8, S=3, K=3, seed=13, kappa=0.0, batch_n=half, block_obs=half)
+    rng = np.random.default_rng(13)
+    theta = P.init + np.c_[rng.normal(0, 0.05, (P.M, 3)), rng.normal(0, 0.01, P.M)]
+    blocks = [np.sort(P.order[b * half:(b + 1) * half]) for b in range(2)]
+    h = 1e-6
+    ell = []
+    for sel in blocks:
+        gb = np.zeros_like(theta)
+        for m in range(P.M):
+            for a in range(4):
+                tp, tm = theta.copy(), theta.copy()
+                tp[m, a] += h
+                tm[m, a] -= h
+                gb[m, a] = (_iid_loss(P, tp, sel) - _iid_loss(P, tm, sel)) / (2 * h)
+        ell.append(gb)
+    want = 0.5 * np.mean((ell[0] - ell[1]) ** 2)
+    _, G, _ = O.log_posterior(P, theta)
+    for eps in (1e-4, 3e-3):
+        for sel in blocks:
+            _, g, _ = O.log_posterior(P, theta, sel)
+            assert abs(O.grad_noise_ratio(g, G, eps) - eps * want) <= 1e-6 * eps * want
+
+
+def test_mlp_tau_gradient_by_finite_differences():
+    net = random_net(H=16, scale=1.0, seed=4)
+    rng = np.random.default_rng(4)
+    src = np.concatenate([rng.uniform(-10, 10, (25, 2)), rng.uniform(2, 15, (25, 1))], 1)
+    rcv = np.concatenate([rng.uniform(-30, 30, (25, 2)), np.zeros((25, 1))], 1)
+    tau, dtau = O.mlp_tau(src, rcv, net)
+    h = 1e-5
+    for a in range(3):
+        sp, sm = src.copy(), src.copy()
+        sp[:, a] += h
+        sm[:, a] -= h
+        fd = (O.mlp_tau(sp, rcv, net)[0] - O.mlp_tau(sm, rcv, net)[0]) / (2 * h)
+        assert np.allclose(dtau[:, a], fd, rtol=1e-7, atol=1e-10)
+    # T = r tau with its Jacobian split into the geometric and the network part
+    T, dT = O.tt_mlp(src, rcv, net)
+    d = src - rcv
+    r = np.sqrt((d * d).sum(1))
+    assert np.allclose(T, r * tau, rtol=1e-15)
+    assert np.allclose(dT - (tau / r)[:, None] * d, r[:, None] * dtau, rtol=1e-12, atol=1e-14)
+
+
 # ---------------------------------------------------------------- SGLD
 def test_sgld_stationary_law_on_gaussian_target():
     # theta' = theta + eps * (-h (theta - mu)) + sqrt(2 eps) eta has the exact

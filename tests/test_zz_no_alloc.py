@@ -22,11 +22,12 @@ def _inputs(torch, P, seed):
     return s4, r4
 
 
-@pytest.mark.parametrize("H", [128, 256])
-def test_no_alloc_matches_allocating_entry_point_twice(H):
+@pytest.mark.parametrize("H,kind", [(128, "config"), (256, "config"), (256, "strong")])
+def test_no_alloc_matches_allocating_entry_point_twice(H, kind):
     torch = pytest.importorskip("torch")
     torch.cuda.set_device(0)
-    net = binding.Net(binding.TT_MLP, mlp=synth.mlp_weights(H, 4242 + H))
+    w = synth.mlp_weights(H, 4242 + H) if kind == "config" else synth.strong_mlp_weights(H, 4243 + H)
+    net = binding.Net(binding.TT_MLP, mlp=w)
     P = 70001                               # many tiles and a ragged tail
     s4, r4 = _inputs(torch, P, H)
     ref_hi, ref_lo = torch.empty(P, device="cuda"), torch.empty(P, device="cuda")
@@ -47,6 +48,13 @@ def test_no_alloc_matches_allocating_entry_point_twice(H):
         assert float((T - ref_T).abs().max()) <= 1e-6, call
         dJ = (J[:, :3].double() - ref_J[:, :3].double()).norm() / ref_J[:, :3].double().norm()
         assert float(dJ) <= 1e-5, call
+        # the network part r dtau/dx = J - (T / r^2)(x - s) on its own, which the
+        # whole-J check cannot see when the network is small next to the bias
+        d = s4[:, :3].double() - r4[:, :3].double()
+        r2 = (d * d).sum(1, keepdim=True)
+        jn = J[:, :3].double() - (T[:, None] / r2) * d
+        jn_ref = ref_J[:, :3].double() - (ref_T[:, None] / r2) * d
+        assert float((jn - jn_ref).norm() / jn_ref.norm()) <= 1e-5, call
     nd.close()
 
 
@@ -55,6 +63,11 @@ def test_no_alloc_rejects_sizes_beyond_its_limit():
     net = binding.Net(binding.TT_MLP, mlp=synth.mlp_weights(128, 1))
     with pytest.raises(binding.SpiderError) as e:
         binding.spider_tt_pairs_noalloc(net, (1 << 20) + 1, 0, 0, 0)
+    assert e.value.code == -1
+    bad = synth.mlp_weights(128, 2)
+    bad["W"][2][3, 5] = np.nan
+    with pytest.raises(binding.SpiderError) as e:
+        binding.spider_tt_pairs_noalloc(binding.Net(binding.TT_MLP, mlp=bad), 10, 0, 0, 0)
     assert e.value.code == -1
     homo = binding.Net(binding.TT_HOMOGENEOUS, v0=6.0)
     with pytest.raises(binding.SpiderError) as e:

@@ -185,7 +185,9 @@ int spider_sgld_step(spider_ctx *ctx, float eps, uint64_t batch_seed);
  * order, into out; *n_written = count.  Synchronous. */
 int spider_samples(spider_ctx *ctx, double *out, int64_t cap, int64_t *n_written);
 
-/* Current state (M x 4 FP64, caller order) and step counter.  Synchronous. */
+/* Current state (M x 4 FP64, caller order) and step counter.  Synchronous.
+ * theta_0 + dtheta is formed on the device (theta_0 kept in FP64) and copied in
+ * one transfer; a page-locked theta_out is written by DMA. */
 int spider_get_state(spider_ctx *ctx, double *theta_out, int64_t *step_out);
 
 /* Replaces the state and step counter (exact resume: with the same per-step
@@ -246,6 +248,17 @@ int spider_uq(spider_ctx *ctx, const double *truth, double lo_pct, double hi_pct
 /* Waits for queued device work; returns the first device-side error, if any. */
 int spider_sync(spider_ctx *ctx);
 
+/* Limit of every bounded device-side wait of the step (the grid-wide barriers
+ * of the component labelling and of the large-component CG), in ns; the
+ * default is 2 s, at most 600 s.  0 makes a CTA give up as soon as it finds a
+ * barrier incomplete.  A wait that gives up records SPIDER_E_TIMEOUT; every
+ * later kernel of that step, and of the steps queued after it, then returns
+ * without work (theta is left unchanged; the step counter still counts the
+ * steps), until a synchronous call (spider_sync, spider_get_state, ...) reports
+ * the error and clears it.  The tensor-core MLP kernel keeps its own 2 s limit
+ * on its pipeline waits.  Takes effect at the next step. */
+int spider_set_wait_limit_ns(spider_ctx *ctx, uint64_t limit_ns);
+
 /* Per-stage device time of the most recent step or gradient, in ms, from CUDA
  * events on the context stream (enable with spider_set_timing(ctx, 1)):
  * out[0] selection+pair table, [1] travel times (the MLP), [2] residuals and
@@ -255,6 +268,16 @@ int spider_sync(spider_ctx *ctx);
 int spider_set_timing(spider_ctx *ctx, int enable);
 int spider_last_timing(spider_ctx *ctx, float out_ms[5], int64_t *pairs,
                        int64_t *n_obs, int32_t *pcg_iters);
+
+/* Device time of each part of the most recent timed step or gradient, in ms
+ * (CUDA events on the context stream; zeros while timing is off):
+ * out[0] selection + pair table, [1] travel times, [2] residuals and u = B^T r
+ * (k_resid), [3] merge of u over blocks sharing a pair (k_merge_rhs),
+ * [4] whitening solve (matrix, components, solvers), [5] q = Sigma^-1 r and
+ * per-node sums (k_final), [6] scaled dlogp/dT onto pairs (k_merge_s),
+ * [7] centroid, [8] priors + update per event (k_event), [9] log posterior.
+ * *touched_events: events with at least one pair in the minibatch. */
+int spider_last_kernel_timing(spider_ctx *ctx, float out_ms[10], int64_t *touched_events);
 
 /* Debug views of the last evaluation (synchronous):
  * spider_debug_blocks: selected block ids in selection order (int64, cap);
@@ -274,7 +297,8 @@ int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
 /* Facts about a context (synchronous), out[0..n): [0] sub-problems,
  * [1] 1 if the SGLD step runs as a captured CUDA graph, [2] blocks per
  * minibatch step, [3] blocks in total, [4] pairs in total, [5] events,
- * [6] observations, [7] connected components of the last minibatch graph. */
+ * [6] observations, [7] connected components of the last minibatch graph,
+ * [8] block-local nodes (occurrences of pairs in blocks) in total. */
 int spider_info(spider_ctx *ctx, int64_t *out, int32_t n);
 
 /* Sampler diagnostics of Sec. 3.6 at the current state, accumulated in FP64 on

@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
         "spider_uq": (C.c_int, [vp, pd, C.c_double, C.c_double, pd, pd, pd, pd]),
         "spider_sync": (C.c_int, [vp]),
         "spider_set_timing": (C.c_int, [vp, C.c_int]),
+        "spider_set_wait_limit_ns": (C.c_int, [vp, u64]),
+        "spider_last_kernel_timing": (C.c_int, [vp, pf, pi64]),
         "spider_last_timing": (C.c_int, [vp, pf, pi64, pi64, C.POINTER(i32)]),
         "spider_debug_blocks": (C.c_int, [vp, pi64, i64, pi64]),
         "spider_debug_obs": (C.c_int, [vp, pi64, pf, pf, i64, pi64]),
@@ -277,9 +279,16 @@ class Context:
         _check(load_library().spider_samples(self.h, _ptr(out, C.c_double), cap, C.byref(n)), self.h)
         return out[: n.value]
 
-    def spider_get_state(self):
-        th = np.empty((self.M, 4), np.float64)
+    def spider_get_state(self, out_ptr: Optional[int] = None):
+        """(theta M x 4 FP64 in the caller's order, step).  With out_ptr (the
+        address of a host buffer of M x 4 doubles, e.g. page-locked memory) the
+        state is written there and None is returned in place of the array."""
         st = C.c_int64()
+        if out_ptr is not None:
+            _check(load_library().spider_get_state(self.h, C.cast(C.c_void_p(out_ptr), C.POINTER(C.c_double)),
+                                                   C.byref(st)), self.h)
+            return None, st.value
+        th = np.empty((self.M, 4), np.float64)
         _check(load_library().spider_get_state(self.h, _ptr(th, C.c_double), C.byref(st)), self.h)
         return th, st.value
 
@@ -338,6 +347,19 @@ class Context:
     def spider_sync(self):
         _check(load_library().spider_sync(self.h), self.h)
 
+    def spider_last_kernel_timing(self):
+        """Per-kernel device ms of the last timed evaluation (see include/spider.h)
+        and the number of events the minibatch touched."""
+        ms = (C.c_float * 10)()
+        ev = C.c_int64()
+        _check(load_library().spider_last_kernel_timing(self.h, ms, C.byref(ev)), self.h)
+        names = ["select_pairs", "travel_time", "k_resid", "k_merge_rhs", "whitening", "k_final",
+                 "k_merge_s", "centroid", "k_event", "logpost"]
+        return dict(zip(names, list(ms))), ev.value
+
+    def spider_set_wait_limit_ns(self, limit_ns: int):
+        _check(load_library().spider_set_wait_limit_ns(self.h, int(limit_ns)), self.h)
+
     def spider_set_timing(self, on: bool):
         _check(load_library().spider_set_timing(self.h, 1 if on else 0), self.h)
 
@@ -353,9 +375,10 @@ class Context:
         _check(load_library().spider_set_tuning(self.h, _ptr(arr, C.c_int32), arr.size), self.h)
 
     def spider_info(self):
-        out = np.zeros(8, np.int64)
-        _check(load_library().spider_info(self.h, _ptr(out, C.c_int64), 8), self.h)
-        keys = ["n_sub", "graph", "blocks_per_step", "blocks", "pairs", "events", "obs", "components"]
+        out = np.zeros(9, np.int64)
+        _check(load_library().spider_info(self.h, _ptr(out, C.c_int64), 9), self.h)
+        keys = ["n_sub", "graph", "blocks_per_step", "blocks", "pairs", "events", "obs", "components",
+                "local_nodes"]
         return dict(zip(keys, (int(x) for x in out)))
 
     def spider_diagnostics(self, batch_seed: int, eps: float):

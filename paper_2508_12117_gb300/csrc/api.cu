@@ -40,7 +40,15 @@ struct spider_ctx {
   int64_t n_samples = 0;           // samples written so far (ring of sample_cap)
   int64_t last_nb = 0;
   bool timing = false;
-  cudaEvent_t ev[6] = {};
+  uint64_t wait_ns = 2000000000ull; // limit of the bounded device-side waits
+  double* state_dev = nullptr;     // M x 4 FP64 read-back buffer (caller order)
+  float4* grad_dev = nullptr;      // M gradient read-back buffer (caller order)
+  int grid_ev = 1;                 // CTAs of the read-back kernels
+  // stage events of a timed evaluation: start, after selection + pair table,
+  // travel times, k_resid, k_merge_rhs, whitening, k_final, k_merge_s,
+  // centroid, k_event, end
+  static constexpr int kEv = 11;
+  cudaEvent_t ev[kEv] = {};
   float last_ms[5] = {0, 0, 0, 0, 0};
   bool have_timing = false;
 };
@@ -227,10 +235,10 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed) 
   TTOut out{v.T2, v.J};
   TRY(launch_tt(c->net, src, out, c->num_sms, c->tt_scratch, st, c->knobs[2]));
   if (timed) TRY(cudaEventRecord(c->ev[2], st));
-  TRY(launch_resid(v, n_b, c->gu, st));
+  TRY(launch_resid(v, n_b, c->gu, st, timed ? &c->ev[3] : nullptr));
   TRY(launch_pcg(v, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
-  if (timed) TRY(cudaEventRecord(c->ev[3], st));
-  TRY(launch_finish(v, n_b, c->gu, logpost, st));
+  if (timed) TRY(cudaEventRecord(c->ev[5], st));
+  TRY(launch_finish(v, n_b, c->gu, logpost, st, timed ? &c->ev[6] : nullptr));
 #undef TRY
   return cudaSuccess;
 }
@@ -251,6 +259,7 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
   hp.mode = mode;
   hp.full = full ? 1 : 0;
   hp.sample_slot = -1;
+  hp.wait_ns = c->wait_ns;
   if (mode == 1 && ((c->step + 1) % cfg.thin) == 0 && v.sample_cap > 0) hp.sample_slot = c->n_samples % v.sample_cap;
   {
     const double t = (double)(c->step + 1);
@@ -287,7 +296,7 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
     const cudaError_t e = step_sequence(c, n_b, mode == 0, c->timing);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
   }
-  if (c->timing) CK(c, cudaEventRecord(c->ev[4], st));
+  if (c->timing) CK(c, cudaEventRecord(c->ev[spider_ctx::kEv - 1], st));
   if (mode == 1) {
     c->step += 1;
     if (hp.sample_slot >= 0) c->n_samples += 1;
@@ -422,6 +431,8 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   } while (0)
   UP(th0_hi, h_hi.data(), M);
   UP(th0_lo, h_lo.data(), M);
+  UP(th0_d, P.th0.data(), 4 * M);
+  UP(ev_out, P.ev_old.data(), M);
   UP(ev_caller, P.ev_local.data(), M);
   {
     // sub-problem tables
@@ -547,6 +558,14 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   AL(dblk, NB);
   AL(dred, 4 * kMaxGrid);
   AL(dout, 8);
+  {
+    double* sd = nullptr;
+    float4* gd = nullptr;
+    if ((e = dalloc(L, &sd, 4 * M))) return bail(cuda_fail(c, e, "alloc read-back"));
+    if ((e = dalloc(L, &gd, M))) return bail(cuda_fail(c, e, "alloc read-back"));
+    c->state_dev = sd;
+    c->grad_dev = gd;
+  }
   const int64_t cap = c->cfg.sample_cap;
   AL(samples, (size_t)std::max<int64_t>(cap, 1) * M);
   if (c->cfg.update != SPIDER_UPDATE_SGLD) {
@@ -580,6 +599,7 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
                              (float)(1.0 / (cfg->sig_c[2] * cfg->sig_c[2])), (float)(1.0 / (cfg->sig_c[3] * cfg->sig_c[3])));
   v.cen_grid = (int)std::min<int64_t>((int64_t)(M + 255) / 256, (int64_t)std::min(kMaxGrid, 4 * c->num_sms));
   c->gu = std::min(kMaxGrid, 4 * c->num_sms);
+  c->grid_ev = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(M + 255) / 256, 8 * c->num_sms));
 
   if ((e = upload_net(net, cfg->precision, &c->net, L, st))) return bail(cuda_fail(c, e, "network upload"));
   c->net.err = v.counters + kCntError;
@@ -596,7 +616,7 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   c->ev_old = std::move(P.ev_old);
   c->ord = std::move(P.ord);
   c->th0 = std::move(P.th0);
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < spider_ctx::kEv; ++i)
     if ((e = cudaEventCreate(&c->ev[i]))) return bail(cuda_fail(c, e, "event"));
   if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "create sync"));
   *out = c;
@@ -686,18 +706,16 @@ int spider_grad_logpost(spider_ctx* c, uint64_t batch_seed, float* grad_out, dou
   int rc = evaluate(c, batch_seed, 0, 0.f);
   if (rc) return rc;
   const size_t M = c->v.M;
-  std::vector<float4> g(grad_out ? M : 0);
   double lp = 0.0;
-  if (grad_out) CK(c, cudaMemcpyAsync(g.data(), c->v.grad, M * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  if (grad_out) {
+    // reordered to the caller's events on the device, then one copy
+    CK(c, launch_grad_out(c->v, c->grad_dev, c->grid_ev, c->stream));
+    CK(c, cudaMemcpyAsync(grad_out, c->grad_dev, M * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  }
   if (logpost_out) CK(c, cudaMemcpyAsync(&lp, c->v.dout + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   rc = check_device_error(c);
   if (rc) return rc;
-  if (grad_out)
-    for (size_t m = 0; m < M; ++m) {
-      float* o = grad_out + 4 * (size_t)c->ev_old[m];
-      o[0] = g[m].x; o[1] = g[m].y; o[2] = g[m].z; o[3] = g[m].w;
-    }
   if (logpost_out) *logpost_out = lp;
   return SPIDER_OK;
 }
@@ -720,19 +738,12 @@ int spider_samples(spider_ctx* c, double* out, int64_t cap, int64_t* n_written) 
   const int64_t n = std::min<int64_t>(have, cap);
   const int64_t first = c->n_samples - have;     // oldest kept sample index
   const size_t M = c->v.M;
-  std::vector<float4> buf(M);
   for (int64_t s = 0; s < n; ++s) {
     const int64_t slot = (first + s) % c->v.sample_cap;
-    CK(c, cudaMemcpy(buf.data(), c->v.samples + slot * M, M * sizeof(float4), cudaMemcpyDeviceToHost));
-    double* o = out + (size_t)s * 4 * M;
-    for (size_t m = 0; m < M; ++m) {
-      double* x = o + 4 * (size_t)c->ev_old[m];
-      const double* t = &c->th0[4 * m];
-      x[0] = t[0] + (double)buf[m].x;
-      x[1] = t[1] + (double)buf[m].y;
-      x[2] = t[2] + (double)buf[m].z;
-      x[3] = t[3] + (double)buf[m].w;
-    }
+    CK(c, launch_state_out(c->v, c->v.samples + slot * M, c->state_dev, c->grid_ev, c->stream));
+    CK(c, cudaMemcpyAsync(out + (size_t)s * 4 * M, c->state_dev, 4 * M * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
   }
   *n_written = n;
   return SPIDER_OK;
@@ -741,20 +752,15 @@ int spider_samples(spider_ctx* c, double* out, int64_t cap, int64_t* n_written) 
 int spider_get_state(spider_ctx* c, double* theta_out, int64_t* step_out) {
   if (!c) return SPIDER_E_INVAL;
   const size_t M = c->v.M;
-  std::vector<float4> buf(M);
-  CK(c, cudaMemcpyAsync(buf.data(), c->v.dth, M * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  if (theta_out) {
+    // theta_0 + dtheta formed on the device in FP64 and the caller's order:
+    // one device-to-host copy (a page-locked theta_out is copied by DMA)
+    CK(c, launch_state_out(c->v, c->v.dth, c->state_dev, c->grid_ev, c->stream));
+    CK(c, cudaMemcpyAsync(theta_out, c->state_dev, 4 * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
   CK(c, cudaStreamSynchronize(c->stream));
   int rc = check_device_error(c);
   if (rc) return rc;
-  if (theta_out)
-    for (size_t m = 0; m < M; ++m) {
-      double* x = theta_out + 4 * (size_t)c->ev_old[m];
-      const double* t = &c->th0[4 * m];
-      x[0] = t[0] + (double)buf[m].x;
-      x[1] = t[1] + (double)buf[m].y;
-      x[2] = t[2] + (double)buf[m].z;
-      x[3] = t[3] + (double)buf[m].w;
-    }
   if (step_out) *step_out = c->step;
   return SPIDER_OK;
 }
@@ -950,6 +956,12 @@ int spider_sync(spider_ctx* c) {
   return check_device_error(c);
 }
 
+int spider_set_wait_limit_ns(spider_ctx* c, uint64_t limit_ns) {
+  if (!c || limit_ns > 600000000000ull) return SPIDER_E_INVAL;
+  c->wait_ns = limit_ns;
+  return SPIDER_OK;
+}
+
 int spider_set_timing(spider_ctx* c, int enable) {
   if (!c) return SPIDER_E_INVAL;
   c->timing = enable != 0;
@@ -964,13 +976,28 @@ int spider_last_timing(spider_ctx* c, float out_ms[5], int64_t* pairs, int64_t* 
   if (out_ms) {
     for (int i = 0; i < 5; ++i) out_ms[i] = 0.f;
     if (c->have_timing) {
-      for (int i = 0; i < 4; ++i) CK(c, cudaEventElapsedTime(&out_ms[i], c->ev[i], c->ev[i + 1]));
-      CK(c, cudaEventElapsedTime(&out_ms[4], c->ev[0], c->ev[4]));
+      const int a[4] = {0, 1, 2, 5}, b[4] = {1, 2, 5, spider_ctx::kEv - 1};
+      for (int i = 0; i < 4; ++i) CK(c, cudaEventElapsedTime(&out_ms[i], c->ev[a[i]], c->ev[b[i]]));
+      CK(c, cudaEventElapsedTime(&out_ms[4], c->ev[0], c->ev[spider_ctx::kEv - 1]));
     }
   }
   if (pairs) *pairs = cnt[kCntPairs];
   if (n_obs) *n_obs = cnt[kCntObs];
   if (pcg_iters) *pcg_iters = cnt[kCntIters] > cnt[kCntCompIters] ? cnt[kCntIters] : cnt[kCntCompIters];
+  return SPIDER_OK;
+}
+
+int spider_last_kernel_timing(spider_ctx* c, float out_ms[10], int64_t* touched_events) {
+  if (!c) return SPIDER_E_INVAL;
+  int32_t cnt[kCntSlots] = {0};
+  CK(c, cudaMemcpyAsync(cnt, c->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (out_ms) {
+    for (int i = 0; i < 10; ++i) out_ms[i] = 0.f;
+    if (c->have_timing)
+      for (int i = 0; i < 10; ++i) CK(c, cudaEventElapsedTime(&out_ms[i], c->ev[i], c->ev[i + 1]));
+  }
+  if (touched_events) *touched_events = cnt[kCntEvents];
   return SPIDER_OK;
 }
 
@@ -1034,9 +1061,9 @@ int spider_info(spider_ctx* c, int64_t* out, int32_t n) {
   int32_t cnt[kCntSlots] = {0};
   CK(c, cudaMemcpyAsync(cnt, c->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  const int64_t vals[8] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
-                           cnt[kCntComps]};
-  for (int32_t i = 0; i < n && i < 8; ++i) out[i] = vals[i];
+  const int64_t vals[9] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
+                           cnt[kCntComps], c->v.Q};
+  for (int32_t i = 0; i < n && i < 9; ++i) out[i] = vals[i];
   return SPIDER_OK;
 }
 

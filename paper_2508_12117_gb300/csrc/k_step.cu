@@ -295,7 +295,11 @@ __device__ __forceinline__ uint64_t gtimer() {
   return t;
 }
 
-__device__ bool grid_barrier(int32_t* counters) {
+// The limit comes from the step parameters (spider_set_wait_limit_ns); a limit
+// of 0 gives up at once whenever the barrier is not complete on arrival.  The
+// error flag is checked on the first spin and every 1024 spins after it, so a
+// CTA that finds another CTA's error leaves without waiting out its limit.
+__device__ bool grid_barrier(int32_t* counters, uint64_t limit_ns) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -309,13 +313,11 @@ __device__ bool grid_barrier(int32_t* counters) {
       __threadfence();
       atomicAdd(&counters[kCntBarGen], 1);
     } else {
-      uint64_t t0 = 0;
-      for (uint32_t n = 1; *gen == g0; ++n) {
+      const uint64_t t0 = gtimer();
+      for (uint32_t n = 0; *gen == g0; ++n) {
         if ((n & 1023u) == 0) {
           if (((volatile int32_t*)counters)[kCntError] != 0) { ok = 0; break; }
-          const uint64_t t = gtimer();
-          if (t0 == 0) t0 = t;
-          else if (t - t0 > 2000000000ull) {
+          if (gtimer() - t0 >= limit_ns) {
             set_error(counters, SPIDER_E_TIMEOUT);
             ok = 0;
             break;
@@ -327,6 +329,22 @@ __device__ bool grid_barrier(int32_t* counters) {
   }
   __syncthreads();
   return ok != 0;
+}
+
+// A kernel that runs after a bounded wait returns at once when an earlier
+// kernel of the step recorded an error: the tables it would read (component
+// labels, work lists) may be incomplete.
+__device__ __forceinline__ bool aborted(const StepView& v) {
+  return *((volatile const int32_t*)v.counters + kCntError) != 0;
+}
+
+// the same test taken once per CTA, for kernels with block-wide barriers
+__device__ __forceinline__ bool aborted_cta(const StepView& v) {
+  __shared__ int a;
+  __syncthreads();
+  if (threadIdx.x == 0) a = aborted(v) ? 1 : 0;
+  __syncthreads();
+  return a != 0;
 }
 
 // Fixed-order sum of G partials (every CTA computes the same value).
@@ -492,6 +510,7 @@ __global__ void k_cc_local(StepView v) {
 
 __global__ void __launch_bounds__(512) k_cc(StepView v, int64_t n_b) {
   __shared__ int any;
+  if (aborted_cta(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
   int32_t* flags = v.scan_part;          // one flag per round
@@ -501,7 +520,7 @@ __global__ void __launch_bounds__(512) k_cc(StepView v, int64_t n_b) {
   }
   for (int i = gtid; i < kCcRounds; i += gstride) flags[i] = 0;
   for (int i = gtid; i < kCqBins + 4; i += gstride) v.chist[i] = 0;
-  if (!grid_barrier(v.counters)) return;
+  if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
   int round = 0;
   for (; round < kCcRounds; ++round) {
     if (threadIdx.x == 0) any = 0;
@@ -523,9 +542,9 @@ __global__ void __launch_bounds__(512) k_cc(StepView v, int64_t n_b) {
     if (changed) any = 1;
     __syncthreads();
     if (threadIdx.x == 0 && any) flags[round] = 1;
-    if (!grid_barrier(v.counters)) return;
+    if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
     for (int32_t u = gtid; u < P_u; u += gstride) v.lab[u] = cc_root(v.lab, u);
-    if (!grid_barrier(v.counters)) return;
+    if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
     if (((volatile int32_t*)flags)[round] == 0) break;
   }
   if (round == kCcRounds) {
@@ -542,6 +561,7 @@ __global__ void __launch_bounds__(512) k_cc(StepView v, int64_t n_b) {
 
 // roots (ascending) -> component index; sizes in component order
 __global__ void k_cc_roots(StepView v) {
+  if (aborted(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     if (v.lab[u] != u) continue;
@@ -556,6 +576,7 @@ __global__ void k_cc_roots(StepView v) {
 
 // member lists (arbitrary order inside a component; the solver sorts them)
 __global__ void k_cc_fill(StepView v) {
+  if (aborted(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     const int32_t r = v.lab[u];
@@ -571,6 +592,7 @@ __global__ void k_cc_fill(StepView v) {
 // members into place; solver tier per component: one warp (n <= kCompMax and
 // entries <= kCompEnt), one CTA (n <= kCtaMax), else the grid-wide solver
 __global__ void k_cc_place(StepView v) {
+  if (aborted(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     v.members[v.lidx[u]] = u;
@@ -589,6 +611,7 @@ __global__ void k_cc_place(StepView v) {
 // the nodes of the grid-tier components as a list in pair order (bigpos holds
 // their exclusive prefix)
 __global__ void k_big_list(StepView v) {
+  if (aborted(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x)
     if (v.big[u]) v.biglist[v.bigpos[u]] = u;
@@ -654,6 +677,7 @@ __device__ __forceinline__ int bsearch_le(const int32_t* a, int n2, int32_t x) {
 // of the warp tier, [+3] end of the list.
 __global__ void k_corder_scan(StepView v) {
   __shared__ int sm[33];
+  if (aborted_cta(v)) return;
   int carry = 0;
   for (int c = 0; c < kCqBins; c += blockDim.x) {
     const int b = c + threadIdx.x;
@@ -674,6 +698,7 @@ __global__ void k_corder_scan(StepView v) {
 }
 
 __global__ void k_corder_fill(StepView v) {
+  if (aborted(v)) return;
   const int32_t ncomp = v.counters[kCntComps];
   for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x) {
     const int tier = v.ctier[c];
@@ -973,6 +998,10 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
   float* pv = S.it.vec[5];
   float* ap = S.it.vec[6];
   float* dz = S.it.vec[7];
+  if (aborted(v)) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    return;
+  }
   const int32_t w_beg = v.chist[kCqBins + 2], w_end = v.chist[kCqBins + 3];
   int max_iters = 0;
   for (;;) {
@@ -1312,6 +1341,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_comp_solve_cta(StepView v, int 
   __shared__ int smi[33];
   __shared__ int32_t s_k;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (aborted_cta(v)) return;
   const float lam = v.lam;
   const int32_t c_end = v.chist[kCqBins + 2];
   int max_iters = 0;
@@ -1438,6 +1468,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_comp_solve_cta(StepView v, int 
 // update phase: two grid barriers per iteration.
 __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) {
   __shared__ float smr[33];
+  if (aborted_cta(v)) return;
   const int G = gridDim.x;
   const int32_t P_u = v.counters[kCntPairs];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = G * blockDim.x;
@@ -1456,7 +1487,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
   }
   bb = block_sum<float>(bb, smr);
   if (threadIdx.x == 0) red[5 * kMaxGrid + blockIdx.x] = bb;
-  if (!grid_barrier(v.counters)) return;
+  if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
   bb = sum_partials(red + 5 * kMaxGrid, G, smr);
   const float outer_thr = tol * tol * bb;
   int it = 0;
@@ -1493,7 +1524,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
       red[0 * kMaxGrid + blockIdx.x] = rz;
       red[1 * kMaxGrid + blockIdx.x] = rr0;
     }
-    if (!grid_barrier(v.counters)) return;
+    if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
     rz = sum_partials(red + 0 * kMaxGrid, G, smr);
     rr0 = sum_partials(red + 1 * kMaxGrid, G, smr);
     if (rr0 <= outer_thr) break;                 // refined solution is accurate enough
@@ -1520,7 +1551,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
       }
       dot = block_sum<float>(dot, smr);
       if (threadIdx.x == 0) red[2 * kMaxGrid + blockIdx.x] = dot;
-      if (!grid_barrier(v.counters)) return;
+      if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
       const float pap = sum_partials(red + 2 * kMaxGrid, G, smr);
       const float alpha = pap > 0.f ? rz / pap : 0.f;
       float rzn = 0.f, rr = 0.f;
@@ -1540,7 +1571,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
         red[3 * kMaxGrid + blockIdx.x] = rzn;
         red[4 * kMaxGrid + blockIdx.x] = rr;
       }
-      if (!grid_barrier(v.counters)) return;
+      if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
       rzn = sum_partials(red + 3 * kMaxGrid, G, smr);
       rr = sum_partials(red + 4 * kMaxGrid, G, smr);
       ++it;
@@ -1556,7 +1587,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
       v.z[u] = zn.hi;
       v.z_lo[u] = zn.lo;
     }
-    if (!grid_barrier(v.counters)) return;
+    if (!grid_barrier(v.counters, v.prm->wait_ns)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) v.counters[kCntIters] = it;
 }
@@ -1567,6 +1598,7 @@ __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) 
 __global__ void k_final(StepView v) {
   extern __shared__ float smf[];
   __shared__ double smd[33];
+  if (aborted_cta(v)) return;
   float* zh = smf;
   float* zl = zh + v.L_max;
   float* qs = zl + v.L_max;
@@ -1623,6 +1655,7 @@ __global__ void k_final(StepView v) {
 
 // s_p * (N_s/n_s) times (dT/dx_p, 1) into the global pair slots, stamped.
 __global__ void k_merge_s(StepView v) {
+  if (aborted(v)) return;
   const int tag = v.prm->tag;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
@@ -1645,6 +1678,7 @@ __global__ void k_merge_s(StepView v) {
 // events summed in a fixed tree, chunks summed in order
 __global__ void k_cen_chunk(StepView v) {
   __shared__ float smr[33];
+  if (aborted_cta(v)) return;
   const int c = blockIdx.x;
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int32_t m = v.chunk_ev0[c] + threadIdx.x; m < v.chunk_ev0[c + 1]; m += blockDim.x) {
@@ -1660,6 +1694,7 @@ __global__ void k_cen_chunk(StepView v) {
 
 __global__ void k_cen_final(StepView v) {
   __shared__ float smr[33];
+  if (aborted_cta(v)) return;
   const int s = blockIdx.x;
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int32_t c = v.sub_chunk_off[s] + threadIdx.x; c < v.sub_chunk_off[s + 1]; c += blockDim.x) {
@@ -1681,6 +1716,7 @@ __global__ void k_cen_final(StepView v) {
 // mode 0: write grad; mode 1: SGLD theta += eps grad + ns sqrt(2 eps) eta (Sec. 3.2)
 __global__ void k_event(StepView v) {
   __shared__ double smd[33];
+  if (aborted_cta(v)) return;
   const StepParams& pr = *v.prm;
   const int tag = pr.tag, mode = pr.mode;
   const float eps = pr.eps;
@@ -1688,13 +1724,14 @@ __global__ void k_event(StepView v) {
   const float sq = pr.noise_scale * sqrtf(2.0f * eps);
   const uint2 key = seed_key(pr.seed);
   double lp = 0.0;
-  int bad = 0;
+  int bad = 0, touched = 0;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M; m += (int64_t)gridDim.x * blockDim.x) {
     const int sb = v.ev_sub[m];
     const float4 cen = v.sub_cen[sb];
     const float invM = 1.0f / (float)v.sub_nev[sb];
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (v.estamp[m] == tag) {
+      ++touched;
       for (int32_t p = v.pair_off[m], p1 = v.pair_off[m + 1]; p < p1; ++p)
         if (v.pstamp[p] == tag) {
           const float4 c = v.gp[p];
@@ -1761,6 +1798,8 @@ __global__ void k_event(StepView v) {
     }
   }
   if (bad) set_error(v.counters, SPIDER_E_NONFINITE);
+  touched = block_sum<int>(touched, reinterpret_cast<int*>(smd));
+  if (threadIdx.x == 0 && touched) atomicAdd(&v.counters[kCntEvents], touched);
   if (mode == 0) {
     lp = block_sum<double>(lp, smd);
     if (threadIdx.x == 0) v.dred[2 * kMaxGrid + blockIdx.x] = lp;
@@ -1771,6 +1810,7 @@ __global__ void k_event(StepView v) {
 //                     - 1/2 sum_s |mean_s(dtheta)/sigma_c|^2   (constants dropped)
 __global__ void k_logpost(StepView v, int64_t n_b) {
   __shared__ double smd[33];
+  if (aborted_cta(v)) return;
   double quad = 0.0, lp = 0.0;
   for (int64_t t = threadIdx.x; t < n_b; t += blockDim.x) {
     const int sb = v.blk_sub[v.sel[t]];
@@ -1809,6 +1849,28 @@ __global__ void k_diag(StepView v, const float4* __restrict__ g, const float4* _
   }
   acc = block_sum<double>(acc, smd);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// theta = theta_0 + dtheta in FP64, written in the caller's event order (the
+// read-back of spider_get_state / spider_samples); src is the state offset or
+// one stored sample.
+__global__ void k_state_out(StepView v, const float4* __restrict__ src, double* __restrict__ out) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M; m += (int64_t)gridDim.x * blockDim.x) {
+    const float4 d = src[m];
+    const double* t = v.th0_d + 4 * m;
+    double4 o;
+    o.x = t[0] + (double)d.x;
+    o.y = t[1] + (double)d.y;
+    o.z = t[2] + (double)d.z;
+    o.w = t[3] + (double)d.w;
+    reinterpret_cast<double4*>(out)[v.ev_out[m]] = o;
+  }
+}
+
+// the gradient (FP32) in the caller's event order
+__global__ void k_grad_out(StepView v, float4* __restrict__ out) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.M; m += (int64_t)gridDim.x * blockDim.x)
+    out[v.ev_out[m]] = v.grad[m];
 }
 
 __global__ void k_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -1870,9 +1932,12 @@ int pcg_grid(const StepView& v, int num_sms) {
   return g > kMaxGrid ? kMaxGrid : g;
 }
 
-cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st) {
+// ev (or null): events recorded after k_resid and after k_merge_rhs
+cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st, const cudaEvent_t* ev) {
   k_resid<<<(unsigned)n_b, kThreads, resid_smem(v), st>>>(v);
+  if (ev) CK_LAUNCH(cudaEventRecord(ev[0], st));
   if (v.whiten) k_merge_rhs<<<gu, kThreads, 0, st>>>(v);
+  if (ev) CK_LAUNCH(cudaEventRecord(ev[1], st));
   return cudaGetLastError();
 }
 
@@ -1939,12 +2004,18 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
   return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(512), args, 0, st);
 }
 
-cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, cudaStream_t st) {
+// ev (or null): events recorded after k_final, k_merge_s, the centroid, k_event
+cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, cudaStream_t st,
+                          const cudaEvent_t* ev) {
   k_final<<<(unsigned)n_b, kThreads, final_smem(v), st>>>(v);
+  if (ev) CK_LAUNCH(cudaEventRecord(ev[0], st));
   k_merge_s<<<gu, kThreads, 0, st>>>(v);
+  if (ev) CK_LAUNCH(cudaEventRecord(ev[1], st));
   k_cen_chunk<<<v.n_chunks, kThreads, 0, st>>>(v);
   k_cen_final<<<v.n_sub, kThreads, 0, st>>>(v);
+  if (ev) CK_LAUNCH(cudaEventRecord(ev[2], st));
   k_event<<<v.cen_grid, kThreads, 0, st>>>(v);
+  if (ev) CK_LAUNCH(cudaEventRecord(ev[3], st));
   if (logpost) k_logpost<<<1, kThreads, 0, st>>>(v, n_b);
   return cudaGetLastError();
 }
@@ -1952,6 +2023,16 @@ cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, 
 cudaError_t launch_diag(const StepView& v, const float4* g, const float4* G, double* norms, double* part,
                         int grid, cudaStream_t st) {
   k_diag<<<grid, kThreads, 0, st>>>(v, g, G, norms, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_out(const StepView& v, const float4* src, double* out, int grid, cudaStream_t st) {
+  k_state_out<<<grid, kThreads, 0, st>>>(v, src, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_out(const StepView& v, float4* out, int grid, cudaStream_t st) {
+  k_grad_out<<<grid, kThreads, 0, st>>>(v, out);
   return cudaGetLastError();
 }
 

@@ -15,7 +15,8 @@ enum : int {
   kCntBarGen = 5,    // grid barrier generation
   kCntComps = 6,     // connected components of the minibatch graph
   kCntCompIters = 7, // largest CG iteration count of a component solved by one warp
-  kCntSlots = 8
+  kCntEvents = 8,    // events touched by the minibatch (with at least one pair)
+  kCntSlots = 9
 };
 
 // Travel-time network on the device.
@@ -72,6 +73,7 @@ struct StepParams {
   int32_t pad;
   int64_t sample_slot;   // -1: no sample this step
   float bc1, bc2;        // Adam bias corrections 1 / (1 - beta^t)
+  uint64_t wait_ns;      // limit of every bounded device-side wait (grid barriers)
 };
 
 // Step state and tables.
@@ -99,6 +101,8 @@ struct StepView {
   float4* cen_chunk;              // n_chunks
   const float4* th0_hi;
   const float4* th0_lo;
+  const double* th0_d;        // M x 4 theta_0 in FP64 (read-back only)
+  const int32_t* ev_out;      // M: caller's event index (global) of each internal event
   float4* dth;
   const int32_t* ev_caller;   // caller's index of each (internal) event: the noise counter
   const float4* sta_hi;

@@ -291,14 +291,26 @@ int spider_debug_obs(spider_ctx *ctx, int64_t *idx_out, float *r_out, float *q_o
  * connected component is computed independently of how work is spread):
  * knobs[0] CTAs per SM-slot of the per-component warp solver (1..8),
  * knobs[1] of the per-component CTA solver (1..4), knobs[2] CTAs per SM of
- * the FP32 MLP kernel (1..2).  Invalidates the captured step graph. */
+ * the FP32 MLP kernel (1..2), knobs[3] 1 (default): minibatch steps whiten
+ * through the precomputed inverses of the block-local components when they
+ * were built, 0: always through the general component solver.  Invalidates
+ * the captured step graph. */
 int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
 
 /* Facts about a context (synchronous), out[0..n): [0] sub-problems,
  * [1] 1 if the SGLD step runs as a captured CUDA graph, [2] blocks per
  * minibatch step, [3] blocks in total, [4] pairs in total, [5] events,
  * [6] observations, [7] connected components of the last minibatch graph,
- * [8] block-local nodes (occurrences of pairs in blocks) in total. */
+ * [8] block-local nodes (occurrences of pairs in blocks) in total,
+ * [9] 1 if the inverses of the block-local components were precomputed,
+ * [10] 1 if minibatch steps whiten through them, [11] units of pieces that
+ * shared nodes in the last such step, [12] 1 if that step fell back to the
+ * general component solver (a unit beyond the limits of the direct path),
+ * [13] units of that step solved by the last unit pass, [14], [15] SM cycles /
+ * 1024 spent on the units of the CTA pass and of the last pass, [16..30] per
+ * unit pass (one warp, CTA, last) five counters: SM cycles / 1024 in set-up,
+ * the pieces' small inverses, the inverse of S, the refinement rounds, and
+ * the units solved. */
 int spider_info(spider_ctx *ctx, int64_t *out, int32_t n);
 
 /* Sampler diagnostics of Sec. 3.6 at the current state, accumulated in FP64 on

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "pieces.h"
 #include "prep.h"
 #include "spider.h"
 
@@ -36,7 +37,13 @@ struct spider_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_ok = true;
   bool use_graph = true;
-  int32_t knobs[3] = {2, 1, 2};   // see spider_set_tuning
+  int32_t knobs[4] = {2, 1, 2, 1};   // see spider_set_tuning
+  // whitening through precomputed piece inverses (minibatch steps)
+  bool fast = false;               // tables built
+  bool mb_full_sub = false;        // a sub-problem selects all its blocks in a minibatch
+  int cc_grid = 0, clean_grid = 0;
+  int unit_grids[3] = {0, 0, 0};
+  int64_t piece_bytes = 0;
   int64_t n_samples = 0;           // samples written so far (ring of sample_cap)
   int64_t last_nb = 0;
   bool timing = false;
@@ -208,7 +215,9 @@ int check_device_error(spider_ctx* c) {
 }
 
 // The kernels of one evaluation, in stream order (everything a step does).
-cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed) {
+// fast: whiten through the piece inverses, with the general component solver
+// gated on the flag that path raises for units beyond its limits.
+cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed, bool fast) {
   StepView& v = c->v;
   cudaStream_t st = c->stream;
   cudaError_t e;
@@ -236,7 +245,14 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed) 
   TRY(launch_tt(c->net, src, out, c->num_sms, c->tt_scratch, st, c->knobs[2]));
   if (timed) TRY(cudaEventRecord(c->ev[2], st));
   TRY(launch_resid(v, n_b, c->gu, st, timed ? &c->ev[3] : nullptr));
-  TRY(launch_pcg(v, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
+  if (fast) {
+    TRY(launch_whiten_fast(v, n_b, c->cfg.pcg_tol, c->cc_grid, c->unit_grids, c->clean_grid, st));
+    StepView vg = v;
+    vg.gate = v.wfast + kWGeneral;
+    TRY(launch_pcg(vg, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
+  } else {
+    TRY(launch_pcg(v, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
+  }
   if (timed) TRY(cudaEventRecord(c->ev[5], st));
   TRY(launch_finish(v, n_b, c->gu, logpost, st, timed ? &c->ev[6] : nullptr));
 #undef TRY
@@ -250,6 +266,7 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
   const bool batch_full = cfg.batch_n <= 0 || cfg.batch_n >= v.N;
   const bool full = batch_full || (mode == 0 && seed == 0);
   const int64_t n_b = full ? c->nb_full : c->nb_mb;
+  const bool fast = c->fast && c->knobs[3] && !full && !c->mb_full_sub && v.whiten;
   cudaStream_t st = c->stream;
   StepParams hp{};
   hp.seed = seed;
@@ -273,7 +290,7 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
     // capture the step once; relaunch it every step with fresh parameters
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      const cudaError_t e1 = step_sequence(c, n_b, false, false);
+      const cudaError_t e1 = step_sequence(c, n_b, false, false, fast);
       cudaGraph_t g = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(st, &g);
       if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
@@ -293,7 +310,7 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
   if (graphable && c->graph_exec) {
     CK(c, cudaGraphLaunch(c->graph_exec, st));
   } else {
-    const cudaError_t e = step_sequence(c, n_b, mode == 0, c->timing);
+    const cudaError_t e = step_sequence(c, n_b, mode == 0, c->timing, fast);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
   }
   if (c->timing) CK(c, cudaEventRecord(c->ev[spider_ctx::kEv - 1], st));
@@ -343,6 +360,100 @@ void spider_config_default(spider_config* c) {
 }  // extern "C"
 
 namespace {
+
+// Pieces of every block and their inverses (pieces.h), for whitening the
+// minibatch steps; skipped (the general component solver serves every step)
+// when a piece is larger than the device path takes or the inverses would use
+// more than half of the free device memory.  Returns an error code only for a
+// failed CUDA call.
+int build_fast_whitening(spider_ctx* c, const Prep& P) {
+  Pieces T;
+  if (!build_pieces(P, piece_max_nodes(), &T, 0)) return SPIDER_OK;
+  const int64_t inv_floats = T.piece_inv_off[T.G];
+  const int64_t bytes = inv_floats * 4 + P.Q * (2 + 2 + 2 + 4 + 4) + P.N * 2 * 6 + (T.G + 1) * (8 + 4 * 7) +
+                        (P.NB + 1) * 4 +
+                        (int64_t)c->num_sms * whiten_unit_scratch_floats() * 4;
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemGetInfo");
+  if (bytes > (int64_t)(free_b / 2)) return SPIDER_OK;
+  // the shared-memory attribute first: the occupancy query depends on it
+  if (configure_whiten_kernels() != cudaSuccess) {
+    cudaGetLastError();            // this device cannot run the direct path: the general solver serves
+    return SPIDER_OK;
+  }
+  c->cc_grid = piece_cc_grid(c->num_sms);
+  c->clean_grid = whiten_clean_grid(c->num_sms);
+  if (c->cc_grid < 1 || whiten_units_grids(c->num_sms, c->unit_grids) < 1 || c->clean_grid < 1) return SPIDER_OK;
+  auto& L = c->allocs;
+  StepView& v = c->v;
+  cudaStream_t st = c->stream;
+  const size_t G = T.G, Q = P.Q;
+#define UPF(field, src, n)                                                                       \
+  do {                                                                                           \
+    using _T = std::remove_const_t<std::remove_pointer_t<decltype(v.field)>>;                    \
+    _T* _q = nullptr;                                                                            \
+    if ((e = dupload(L, &_q, (const _T*)(src), (n), st))) return cuda_fail(c, e, "upload " #field); \
+    v.field = _q;                                                                                \
+  } while (0)
+#define ALF(field, n)                                                                \
+  do {                                                                               \
+    using _T = std::remove_pointer_t<decltype(v.field)>;                             \
+    _T* _q = nullptr;                                                                \
+    if ((e = dalloc(L, &_q, (n)))) return cuda_fail(c, e, "alloc " #field);          \
+    v.field = _q;                                                                    \
+  } while (0)
+  UPF(blk_piece_off, T.blk_piece_off.data(), P.NB + 1);
+  UPF(node_piece, T.node_piece.data(), Q);
+  UPF(node_ppos, T.node_ppos.data(), Q);
+  UPF(piece_node_off, T.piece_node_off.data(), G + 1);
+  UPF(piece_nodes, T.piece_nodes.data(), Q);
+  UPF(piece_inv_off, T.piece_inv_off.data(), G + 1);
+  UPF(mem_rp, T.mem_rp.data(), Q + 1);
+  UPF(edge_pos, T.edge_pos.data(), T.edge_pos.size());
+  UPF(edge_sw, T.edge_sw.data(), T.edge_sw.size());
+  ALF(owner_b, Q);
+  ALF(plab, G);
+  ALF(pmulti, G);
+  ALF(pcount, G);
+  ALF(unit_of, G);
+  ALF(unit_cnt, G);
+  ALF(unit_off, G + 1);
+  ALF(unit_pieces, G);
+  ALF(unit_pblk, G);
+  ALF(unit_defer, G);
+  ALF(unit_defer2, G);
+  ALF(clean_list, G);
+  ALF(clean_blk, G);
+  ALF(wfast, kWSlots + 64 + 16);
+  ALF(wscratch, (size_t)c->unit_grids[2] * whiten_unit_scratch_floats());
+#undef UPF
+#undef ALF
+  float* inv = nullptr;
+  if ((e = dalloc(L, &inv, (size_t)inv_floats))) return cuda_fail(c, e, "alloc piece inverses");
+  v.piece_inv = inv;
+  // the inverses block by block in chunks of at most 64 M floats
+  const double lam = (double)c->cfg.sigma * c->cfg.sigma / ((double)c->cfg.kappa * c->cfg.kappa);
+  std::vector<float> buf;
+  for (int64_t b0 = 0; b0 < P.NB;) {
+    int64_t b1 = b0 + 1;
+    const int64_t f0 = T.piece_inv_off[T.blk_piece_off[b0]];
+    while (b1 < P.NB && T.piece_inv_off[T.blk_piece_off[b1 + 1]] - f0 <= (int64_t(1) << 26)) ++b1;
+    const int64_t nf = T.piece_inv_off[T.blk_piece_off[b1]] - f0;
+    buf.resize((size_t)std::max<int64_t>(nf, 1));
+    piece_inverses(P, T, lam, b0, b1, buf.data(), 0);
+    if (nf > 0) {
+      if ((e = cudaMemcpyAsync(inv + f0, buf.data(), nf * sizeof(float), cudaMemcpyHostToDevice, st)))
+        return cuda_fail(c, e, "upload piece inverses");
+      if ((e = cudaStreamSynchronize(st))) return cuda_fail(c, e, "upload piece inverses");
+    }
+    b0 = b1;
+  }
+  if ((e = cudaStreamSynchronize(st))) return cuda_fail(c, e, "upload sync");
+  c->piece_bytes = bytes;
+  c->fast = true;
+  return SPIDER_OK;
+}
 
 // Builds a context over a catalog made of n_sub independent sub-problems
 // (a single catalog is one sub-problem); see prepare() for the splits.
@@ -446,6 +557,7 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
       const int64_t want = bfull ? nbs : std::min<int64_t>(nbs, (cfg->batch_n + P.B - 1) / P.B);
       sel_full[s2 + 1] = sel_full[s2] + (int32_t)nbs;
       sel_mb[s2 + 1] = sel_mb[s2] + (int32_t)want;
+      if (!bfull && want == nbs && nbs > 1) c->mb_full_sub = true;
       nobs[s2] = (int32_t)(P.sub_obs_off[s2 + 1] - P.sub_obs_off[s2]);
       nev[s2] = (int32_t)(P.sub_ev_off[s2 + 1] - P.sub_ev_off[s2]);
       ch[s2] = sub_chain[s2];
@@ -612,6 +724,10 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   if (c->pgrid < 1) {
     c->err = "whitening kernel does not fit on the device (block too large)";
     return bail(SPIDER_E_UNSUPPORTED);
+  }
+  if (v.whiten && !(cfg->batch_n <= 0 || cfg->batch_n >= (int64_t)N)) {
+    rc = build_fast_whitening(c, P);
+    if (rc) return bail(rc);
   }
   c->ev_old = std::move(P.ev_old);
   c->ord = std::move(P.ord);
@@ -1041,14 +1157,14 @@ int spider_debug_obs(spider_ctx* c, int64_t* idx_out, float* r_out, float* q_out
 
 int spider_set_tuning(spider_ctx* c, const int32_t* knobs, int32_t n) {
   if (!c || (n > 0 && !knobs)) return SPIDER_E_INVAL;
-  const int32_t lo[3] = {1, 1, 1}, hi[3] = {8, 4, 2};
-  for (int32_t i = 0; i < n && i < 3; ++i)
+  const int32_t lo[4] = {1, 1, 1, 0}, hi[4] = {8, 4, 2, 1};
+  for (int32_t i = 0; i < n && i < 4; ++i)
     if (knobs[i] < lo[i] || knobs[i] > hi[i]) {
       c->err = "tuning knob out of range";
       return SPIDER_E_INVAL;
     }
   CK(c, cudaStreamSynchronize(c->stream));
-  for (int32_t i = 0; i < n && i < 3; ++i) c->knobs[i] = knobs[i];
+  for (int32_t i = 0; i < n && i < 4; ++i) c->knobs[i] = knobs[i];
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
@@ -1061,9 +1177,16 @@ int spider_info(spider_ctx* c, int64_t* out, int32_t n) {
   int32_t cnt[kCntSlots] = {0};
   CK(c, cudaMemcpyAsync(cnt, c->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  const int64_t vals[9] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
-                           cnt[kCntComps], c->v.Q};
-  for (int32_t i = 0; i < n && i < 9; ++i) out[i] = vals[i];
+  int32_t wf[kWSlots + 64 + 16] = {0};
+  if (c->fast) {
+    CK(c, cudaMemcpyAsync(wf, c->v.wfast, sizeof(wf), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  int64_t vals[31] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
+                      cnt[kCntComps], c->v.Q, c->fast ? 1 : 0, c->fast ? (c->mb_full_sub ? 0 : 1) : 0,
+                      wf[kWUnits], wf[kWGeneral], wf[kWBigS], wf[kWCycSm], wf[kWCycBig]};
+  for (int i = 0; i < 15; ++i) vals[16 + i] = wf[kWSlots + 64 + i];
+  for (int32_t i = 0; i < n && i < 31; ++i) out[i] = vals[i];
   return SPIDER_OK;
 }
 

@@ -12,68 +12,13 @@
 #include "kernels.h"
 #include "philox.cuh"
 #include "spider.h"
+#include "step_util.cuh"
 
 namespace spider {
 
 namespace {
 
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ void set_error(int32_t* counters, int code) {
-  atomicCAS(&counters[kCntError], 0, code);
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-wide sum with a fixed reduction tree (deterministic). All threads get it.
-template <typename T>
-__device__ T block_sum(T v, T* sm /* >= 32 */) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) sm[wid] = v;
-  __syncthreads();
-  T t = lane < nw ? sm[lane] : T(0);
-  if (wid == 0) t = warp_sum(t);
-  if (threadIdx.x == 0) sm[0] = t;
-  __syncthreads();
-  T r = sm[0];
-  __syncthreads();
-  return r;
-}
-
-// Exclusive block scan of small integers; returns the prefix, *total = sum.
-__device__ int block_exscan(int v, int* sm /* >= 33 */, int* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  __syncthreads();
-  if (lane == 31) sm[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    int s = lane < nw ? sm[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < nw) sm[lane] = s;  // inclusive per-warp totals
-  }
-  __syncthreads();
-  int warp_base = wid ? sm[wid - 1] : 0;
-  *total = sm[nw - 1];
-  __syncthreads();
-  return warp_base + x - v;
-}
 
 // Sum over the selected occurrences of pair p of vals[q] (block order).
 __device__ __forceinline__ float merge_occ(const StepView& v, int32_t p, int tag, const float* vals) {
@@ -122,14 +67,18 @@ __global__ void k_owner(StepView v) {
   int cnt = 0;
   for (int32_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
     const int32_t p = v.node_pair[q];
-    int32_t qo = -1;
+    int32_t qo = -1, bo = -1;
     int c = 0;
     for (int32_t t = v.inc_off[p], t1 = v.inc_off[p + 1]; t < t1; ++t)
       if (v.blk_stamp[v.inc_b[t]] == tag) {
-        if (qo < 0) qo = v.inc_q[t];
+        if (qo < 0) {
+          qo = v.inc_q[t];
+          bo = v.inc_b[t];
+        }
         ++c;
       }
     v.owner_q[q] = qo;
+    if (v.owner_b) v.owner_b[q] = bo;
     v.multi[q] = (uint8_t)(c > 1);
     cnt += (qo == q);
   }
@@ -287,66 +236,6 @@ __global__ void k_merge_rhs(StepView v) {
 }
 
 // ------------------------------------------------------------------ whitening
-// Software grid barrier for a cooperative launch, with a bounded wait
-// (globaltimer, 2 s): on timeout the error flag is set and the caller returns.
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// The limit comes from the step parameters (spider_set_wait_limit_ns); a limit
-// of 0 gives up at once whenever the barrier is not complete on arrival.  The
-// error flag is checked on the first spin and every 1024 spins after it, so a
-// CTA that finds another CTA's error leaves without waiting out its limit.
-__device__ bool grid_barrier(int32_t* counters, uint64_t limit_ns) {
-  __syncthreads();
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
-    volatile int32_t* gen = counters + kCntBarGen;
-    const int32_t g0 = *gen;
-    __threadfence();
-    const int32_t arrived = atomicAdd(&counters[kCntBarArrive], 1);
-    ok = 1;
-    if (arrived == (int)gridDim.x - 1) {
-      counters[kCntBarArrive] = 0;
-      __threadfence();
-      atomicAdd(&counters[kCntBarGen], 1);
-    } else {
-      const uint64_t t0 = gtimer();
-      for (uint32_t n = 0; *gen == g0; ++n) {
-        if ((n & 1023u) == 0) {
-          if (((volatile int32_t*)counters)[kCntError] != 0) { ok = 0; break; }
-          if (gtimer() - t0 >= limit_ns) {
-            set_error(counters, SPIDER_E_TIMEOUT);
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-// A kernel that runs after a bounded wait returns at once when an earlier
-// kernel of the step recorded an error: the tables it would read (component
-// labels, work lists) may be incomplete.
-__device__ __forceinline__ bool aborted(const StepView& v) {
-  return *((volatile const int32_t*)v.counters + kCntError) != 0;
-}
-
-// the same test taken once per CTA, for kernels with block-wide barriers
-__device__ __forceinline__ bool aborted_cta(const StepView& v) {
-  __shared__ int a;
-  __syncthreads();
-  if (threadIdx.x == 0) a = aborted(v) ? 1 : 0;
-  __syncthreads();
-  return a != 0;
-}
-
 // Fixed-order sum of G partials (every CTA computes the same value).
 __device__ float sum_partials(const float* part, int G, float* sm) {
   float a = 0.f;
@@ -374,8 +263,10 @@ __device__ __forceinline__ BlockRange block_range(const StepView& v, int64_t s) 
 // ---- CSR of the merged minibatch matrix: row u = unique pair, entries in
 // block order then half-edge order (so every sum below has a fixed order).
 // Three-phase exclusive scan of src[0, n) into dst (dst[n] = total), n = *n_dev.
-__global__ void k_scan_a(const int32_t* __restrict__ src, const int32_t* n_dev, int32_t* part) {
+__global__ void k_scan_a(const int32_t* __restrict__ src, const int32_t* n_dev, int32_t* part,
+                         const int32_t* gate) {
   __shared__ int sm[33];
+  if (gate && *gate == 0) return;
   const int64_t n = *n_dev;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t a = blockIdx.x * chunk, b = a + chunk < n ? a + chunk : n;
@@ -385,8 +276,9 @@ __global__ void k_scan_a(const int32_t* __restrict__ src, const int32_t* n_dev, 
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-__global__ void k_scan_b(int32_t* part, int parts) {
+__global__ void k_scan_b(int32_t* part, int parts, const int32_t* gate) {
   __shared__ int sm[33];
+  if (gate && *gate == 0) return;
   int carry = 0;
   for (int c = 0; c < parts; c += blockDim.x) {
     const int i = c + threadIdx.x;
@@ -399,8 +291,10 @@ __global__ void k_scan_b(int32_t* part, int parts) {
   if (threadIdx.x == 0) part[parts] = carry;
 }
 
-__global__ void k_scan_c(const int32_t* src, const int32_t* n_dev, const int32_t* part, int32_t* dst) {
+__global__ void k_scan_c(const int32_t* src, const int32_t* n_dev, const int32_t* part, int32_t* dst,
+                         const int32_t* gate) {
   __shared__ int sm[33];
+  if (gate && *gate == 0) return;
   const int64_t n = *n_dev;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t a = blockIdx.x * chunk, b = a + chunk < n ? a + chunk : n;
@@ -418,6 +312,7 @@ __global__ void k_scan_c(const int32_t* src, const int32_t* n_dev, const int32_t
 
 // entries of every occurrence: neighbour's unique index and sqrt(w_e)
 __global__ void k_fill_rows(StepView v) {
+  if (gated_off(v)) return;
   const BlockRange br = block_range(v, blockIdx.x);
   const uint16_t* he = v.blk_he + 2 * br.e0;
   for (int l = threadIdx.x; l < br.L; l += blockDim.x) {
@@ -477,6 +372,7 @@ __device__ __forceinline__ int lroot_find(const int* par, int x) {
 __global__ void k_cc_local(StepView v) {
   extern __shared__ int par[];
   __shared__ int changed;
+  if (gated_off(v)) return;
   const int s = blockIdx.x;
   const int32_t b = v.sel[s];
   const int32_t q0 = v.blk_node_off[b];
@@ -510,7 +406,7 @@ __global__ void k_cc_local(StepView v) {
 
 __global__ void __launch_bounds__(512) k_cc(StepView v, int64_t n_b) {
   __shared__ int any;
-  if (aborted_cta(v)) return;
+  if (aborted_cta(v) || gated_off(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
   int32_t* flags = v.scan_part;          // one flag per round
@@ -561,7 +457,7 @@ __global__ void __launch_bounds__(512) k_cc(StepView v, int64_t n_b) {
 
 // roots (ascending) -> component index; sizes in component order
 __global__ void k_cc_roots(StepView v) {
-  if (aborted(v)) return;
+  if (aborted(v) || gated_off(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     if (v.lab[u] != u) continue;
@@ -576,7 +472,7 @@ __global__ void k_cc_roots(StepView v) {
 
 // member lists (arbitrary order inside a component; the solver sorts them)
 __global__ void k_cc_fill(StepView v) {
-  if (aborted(v)) return;
+  if (aborted(v) || gated_off(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     const int32_t r = v.lab[u];
@@ -592,7 +488,7 @@ __global__ void k_cc_fill(StepView v) {
 // members into place; solver tier per component: one warp (n <= kCompMax and
 // entries <= kCompEnt), one CTA (n <= kCtaMax), else the grid-wide solver
 __global__ void k_cc_place(StepView v) {
-  if (aborted(v)) return;
+  if (aborted(v) || gated_off(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x) {
     v.members[v.lidx[u]] = u;
@@ -611,7 +507,7 @@ __global__ void k_cc_place(StepView v) {
 // the nodes of the grid-tier components as a list in pair order (bigpos holds
 // their exclusive prefix)
 __global__ void k_big_list(StepView v) {
-  if (aborted(v)) return;
+  if (aborted(v) || gated_off(v)) return;
   const int32_t P_u = v.counters[kCntPairs];
   for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < P_u; u += gridDim.x * blockDim.x)
     if (v.big[u]) v.biglist[v.bigpos[u]] = u;
@@ -677,7 +573,7 @@ __device__ __forceinline__ int bsearch_le(const int32_t* a, int n2, int32_t x) {
 // of the warp tier, [+3] end of the list.
 __global__ void k_corder_scan(StepView v) {
   __shared__ int sm[33];
-  if (aborted_cta(v)) return;
+  if (aborted_cta(v) || gated_off(v)) return;
   int carry = 0;
   for (int c = 0; c < kCqBins; c += blockDim.x) {
     const int b = c + threadIdx.x;
@@ -698,7 +594,7 @@ __global__ void k_corder_scan(StepView v) {
 }
 
 __global__ void k_corder_fill(StepView v) {
-  if (aborted(v)) return;
+  if (aborted(v) || gated_off(v)) return;
   const int32_t ncomp = v.counters[kCntComps];
   for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncomp; c += gridDim.x * blockDim.x) {
     const int tier = v.ctier[c];
@@ -998,7 +894,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_comp_solve(StepView v, int 
   float* pv = S.it.vec[5];
   float* ap = S.it.vec[6];
   float* dz = S.it.vec[7];
-  if (aborted(v)) {
+  if (aborted(v) || gated_off(v)) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     return;
   }
@@ -1341,7 +1237,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_comp_solve_cta(StepView v, int 
   __shared__ int smi[33];
   __shared__ int32_t s_k;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  if (aborted_cta(v)) return;
+  if (aborted_cta(v) || gated_off(v)) return;
   const float lam = v.lam;
   const int32_t c_end = v.chist[kCqBins + 2];
   int max_iters = 0;
@@ -1468,7 +1364,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_comp_solve_cta(StepView v, int 
 // update phase: two grid barriers per iteration.
 __global__ void __launch_bounds__(512) k_pcg(StepView v, int max_it, float tol) {
   __shared__ float smr[33];
-  if (aborted_cta(v)) return;
+  if (aborted_cta(v) || gated_off(v)) return;
   const int G = gridDim.x;
   const int32_t P_u = v.counters[kCntPairs];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = G * blockDim.x;
@@ -1947,9 +1843,9 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
   const int32_t* Pdev = v.counters + kCntPairs;
   const int parts = grid;
   // CSR of the merged minibatch matrix
-  k_scan_a<<<parts, kThreads, 0, st>>>(v.rowlen, Pdev, v.scan_part);
-  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
-  k_scan_c<<<parts, kThreads, 0, st>>>(v.rowlen, Pdev, v.scan_part, v.rowptr);
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.rowlen, Pdev, v.scan_part, v.gate);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts, v.gate);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.rowlen, Pdev, v.scan_part, v.rowptr, v.gate);
   k_fill_rows<<<(unsigned)n_b, kThreads, 0, st>>>(v);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1963,18 +1859,18 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
     if (e != cudaSuccess) return e;
   }
   CK_LAUNCH(cudaMemsetAsync(v.counters + kCntBarArrive, 0, 2 * sizeof(int32_t), st));
-  k_scan_a<<<parts, kThreads, 0, st>>>(v.cslot, Pdev, v.scan_part);
-  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
-  k_scan_c<<<parts, kThreads, 0, st>>>(v.cslot, Pdev, v.scan_part, v.members);
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.cslot, Pdev, v.scan_part, v.gate);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts, v.gate);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.cslot, Pdev, v.scan_part, v.members, v.gate);
   k_cc_roots<<<parts, kThreads, 0, st>>>(v);
-  k_scan_a<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part);
-  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
-  k_scan_c<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part, v.comp_off);
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part, v.gate);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts, v.gate);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.comp_off, v.counters + kCntComps, v.scan_part, v.comp_off, v.gate);
   k_cc_fill<<<parts, kThreads, 0, st>>>(v);
   k_cc_place<<<parts, kThreads, 0, st>>>(v);
-  k_scan_a<<<parts, kThreads, 0, st>>>(v.bigpos, Pdev, v.scan_part);
-  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts);
-  k_scan_c<<<parts, kThreads, 0, st>>>(v.bigpos, Pdev, v.scan_part, v.bigpos);
+  k_scan_a<<<parts, kThreads, 0, st>>>(v.bigpos, Pdev, v.scan_part, v.gate);
+  k_scan_b<<<1, 1024, 0, st>>>(v.scan_part, parts, v.gate);
+  k_scan_c<<<parts, kThreads, 0, st>>>(v.bigpos, Pdev, v.scan_part, v.bigpos, v.gate);
   k_big_list<<<parts, kThreads, 0, st>>>(v);
   k_corder_scan<<<1, 512, 0, st>>>(v);
   k_corder_fill<<<parts, kThreads, 0, st>>>(v);

@@ -38,6 +38,15 @@ cudaError_t launch_state_out(const StepView& v, const float4* src, double* out, 
 cudaError_t launch_grad_out(const StepView& v, float4* out, int grid, cudaStream_t st);
 cudaError_t launch_diag(const StepView& v, const float4* g, const float4* G, double* norms, double* part,
                         int grid, cudaStream_t st);
+// whitening through the precomputed piece inverses (k_whiten.cu)
+int piece_max_nodes();
+int64_t whiten_unit_scratch_floats();   // global scratch per CTA of the unit solver
+cudaError_t configure_whiten_kernels();
+int whiten_units_grids(int num_sms, int grids[3]);
+int piece_cc_grid(int num_sms);
+int whiten_clean_grid(int num_sms);
+cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[3],
+                               int clean_grid, cudaStream_t st);
 // stage-1 outlier mask (k_outlier.cu)
 size_t outlier_scratch_bytes(int n_sub);
 cudaError_t launch_outlier(const StepView& v, int n_sub, float kmad, void* scratch, uint8_t* keep,

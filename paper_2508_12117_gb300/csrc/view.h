@@ -183,6 +183,33 @@ struct StepView {
   double* dblk;      // FP64 sum r^2 per selected block (NB)
   double* dred;      // FP64 diagnostics partials, 4 x kMaxGrid
   double* dout;      // FP64 results: [0] loglik (scaled), [1] logprior, [2] logcen, [3] logpost
+  // whitening through the precomputed piece inverses (null when not built)
+  const int32_t* blk_piece_off;   // NB + 1
+  const uint16_t* node_piece;     // Q: piece of a local node, numbered within its block
+  const uint16_t* node_ppos;      // Q: position of a local node inside its piece
+  const int32_t* piece_node_off;  // G + 1
+  const uint16_t* piece_nodes;    // Q: block-local index of each piece member
+  const int64_t* piece_inv_off;   // G + 1
+  const float* piece_inv;         // (lambda I + B^T B)^-1 of every piece, n x n each
+  const int32_t* mem_rp;          // Q + 1: edges of each member (piece_nodes order)
+  const uint16_t* edge_pos;       // 2N: position of the other end inside the piece
+  const float* edge_sw;           // 2N: sqrt w of the edge
+  int32_t* owner_b;               // Q: block of the owner occurrence (per step)
+  int32_t* plab;                  // G: piece labels of the selected pieces (per step)
+  uint8_t* pmulti;                // G: the piece has a node shared with another selected block
+  int32_t* pcount;                // G: pieces per unit, at the unit's root piece
+  int32_t* unit_of;               // G: unit of a root piece
+  int32_t* unit_cnt;              // [G]: pieces per unit (fill cursor afterwards)
+  int32_t* unit_off;              // [G + 1]
+  int32_t* unit_pieces;           // [G]
+  int32_t* unit_pblk;             // [G]: block of each entry of unit_pieces
+  int32_t* unit_defer;            // [G]: units deferred from the one-warp pass to the CTA pass
+  int32_t* unit_defer2;           // [G]: units deferred from the CTA pass to the last pass
+  int32_t* clean_list;            // [G]: pieces of the step with no shared node
+  int32_t* clean_blk;             // [G]: their blocks
+  int32_t* wfast;                 // [kWSlots] unit count, unit cursor, fallback flag, rounds
+  float* wscratch;                // per CTA of the unit solver: S^-1 and the pieces' small inverses
+  const int32_t* gate;            // non-null: the general solver runs only while *gate != 0
   float4* samples;
   float4* mom1;      // Adam first moment (M), null otherwise
   float4* mom2;      // pSGLD / Adam second moment (M), null for SGLD
@@ -200,6 +227,21 @@ struct StepView {
 };
 
 constexpr int kMaxGrid = 4096;
+// wfast[] slots of the piece-inverse whitening
+enum : int {
+  kWUnits = 0, kWCursor = 1, kWGeneral = 2, kWRounds = 3,
+  kWBigS = 4,      // units solved by the second pass (large shared-node sets)
+  kWCycSm = 5,     // SM cycles / 1024 spent on units of the first pass
+  kWCycBig = 6,    // the same for the second pass
+  kWDefer = 7,     // units deferred to the second pass
+  kWCursor2 = 8,   // work cursor of the second pass
+  kWClean = 9,     // single pieces of the step (no shared node)
+  kWCursorC = 10,  // work cursor of the single-piece solver
+  kWCursor0 = 11,  // work cursor of the one-warp unit pass
+  kWDefer2 = 12,   // units deferred from the CTA pass to the last pass
+  kWCycW = 13,     // SM cycles / 1024 spent on units of the one-warp pass
+  kWSlots = 16
+};
 constexpr int kCenChunk = 4096;   // events per centroid partial sum
 
 }  // namespace spider

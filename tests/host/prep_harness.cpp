@@ -46,3 +46,36 @@ extern "C" int prep_get(const char* name, void* out) {
   else return -1;
   return 0;
 }
+
+// ---- block-local pieces and their inverses (pieces.cpp) ----
+#include "pieces.h"
+
+static spider::Pieces g_pieces;
+static std::vector<float> g_inv;
+
+extern "C" int pieces_run(int max_n, double lam, int64_t* sizes) {
+  if (!spider::build_pieces(g_prep, max_n, &g_pieces, 2)) return 1;
+  const spider::Pieces& T = g_pieces;
+  g_inv.assign((size_t)T.piece_inv_off[T.G], 0.f);
+  spider::piece_inverses(g_prep, T, lam, 0, g_prep.NB, g_inv.data(), 2);
+  int64_t s[3] = {T.G, T.max_n, T.piece_inv_off[T.G]};
+  std::memcpy(sizes, s, sizeof(s));
+  return 0;
+}
+
+extern "C" int pieces_get(const char* name, void* out) {
+  const spider::Pieces& T = g_pieces;
+  std::string n(name);
+  if (n == "blk_piece_off") cp(T.blk_piece_off, out);
+  else if (n == "node_piece") cp(T.node_piece, out);
+  else if (n == "node_ppos") cp(T.node_ppos, out);
+  else if (n == "piece_node_off") cp(T.piece_node_off, out);
+  else if (n == "piece_nodes") cp(T.piece_nodes, out);
+  else if (n == "piece_inv_off") cp(T.piece_inv_off, out);
+  else if (n == "inv") cp(g_inv, out);
+  else if (n == "mem_rp") cp(T.mem_rp, out);
+  else if (n == "edge_pos") cp(T.edge_pos, out);
+  else if (n == "edge_sw") cp(T.edge_sw, out);
+  else return -1;
+  return 0;
+}

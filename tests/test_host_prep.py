@@ -23,12 +23,15 @@ def harness(tmp_path_factory):
     cmd = ["g++", "-O2", "-fPIC", "-shared", "-std=c++17", "-pthread", "-ffp-contract=off",
            "-I", os.path.join(ROOT, "include"), "-I", CSRC,
            os.path.join(ROOT, "tests", "host", "prep_harness.cpp"), os.path.join(CSRC, "prep.cpp"),
-           "-o", so]
+           os.path.join(CSRC, "pieces.cpp"), "-o", so]
     subprocess.run(cmd, check=True, capture_output=True)
     L = C.CDLL(so)
     L.prep_run.restype = C.c_int
     L.prep_get.restype = C.c_int
     L.prep_error.restype = C.c_char_p
+    L.pieces_run.restype = C.c_int
+    L.pieces_run.argtypes = [C.c_int, C.c_double, C.c_void_p]
+    L.pieces_get.restype = C.c_int
     return L
 
 
@@ -166,3 +169,84 @@ def test_prep_rejects_bad_input(harness):
     assert run_prep(harness, bad)[0] == -1
     rc, msg, _ = run_prep(harness, cat, block_obs=0)
     assert rc == -1
+
+
+def _pieces(L, R, lam, max_n=512):
+    sizes = np.zeros(3, np.int64)
+    assert L.pieces_run(max_n, lam, sizes.ctypes.data_as(C.c_void_p)) == 0
+    G, _, ninv = (int(x) for x in sizes)
+    spec = dict(blk_piece_off=(R["NB"] + 1, np.int32), node_piece=(R["Q"], np.uint16),
+                node_ppos=(R["Q"], np.uint16), piece_node_off=(G + 1, np.int32),
+                piece_nodes=(R["Q"], np.uint16), piece_inv_off=(G + 1, np.int64), inv=(ninv, np.float32),
+                mem_rp=(R["Q"] + 1, np.int32), edge_pos=(2 * R["N"], np.uint16), edge_sw=(2 * R["N"], np.float32))
+    out = dict(G=G)
+    for name, (n, dt) in spec.items():
+        arr = np.empty(max(n, 1), dt)
+        assert L.pieces_get(name.encode(), arr.ctypes.data_as(C.c_void_p)) == 0
+        out[name] = arr[:n]
+    return out
+
+
+@pytest.mark.parametrize("block_obs", [4096, 700])
+def test_pieces_are_block_components_with_exact_inverses(harness, block_obs):
+    """Pieces are exactly the connected components of each block's local graph
+    (scipy), numbered by smallest member, and each stored inverse is
+    (lambda I + B^T B)^-1 of its piece, built here element by element from the
+    block's observations and inverted by numpy, to FP32 rounding."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    s = synth.scaled_spec(2, 1500, n_faults=2, region_km=10.0)
+    cat = synth.make_catalog(s)
+    rc, msg, R = run_prep(harness, cat, block_obs=block_obs)
+    assert rc == 0, msg
+    lam = 0.005 ** 2 / 0.03 ** 2
+    T = _pieces(harness, R, lam)
+    bno, bpo = R["blk_node_off"], T["blk_piece_off"]
+    assert bpo[-1] == T["G"] and T["piece_node_off"][-1] == R["Q"]
+    w = R["obs_sw"].astype(np.float64) ** 2
+    worst = 0.0
+    for b in range(R["NB"]):
+        e0, e1 = b * R["B"], min(R["N"], (b + 1) * R["B"])
+        q0, q1 = bno[b], bno[b + 1]
+        L_ = q1 - q0
+        li = (R["obs_l"][e0:e1] & 0xFFFF).astype(np.int64)
+        lj = (R["obs_l"][e0:e1] >> 16).astype(np.int64)
+        nc, lab = connected_components(coo_matrix((np.ones(e1 - e0), (li, lj)), shape=(L_, L_)),
+                                       directed=False)
+        assert bpo[b + 1] - bpo[b] == nc
+        # numbering by smallest member: relabel scipy's labels in order of first occurrence
+        first = {}
+        for l in range(L_):
+            first.setdefault(int(lab[l]), len(first))
+        want_piece = np.array([first[int(x)] for x in lab])
+        assert np.array_equal(T["node_piece"][q0:q1], want_piece)
+        for c in range(nc):
+            g = bpo[b] + c
+            mem = T["piece_nodes"][T["piece_node_off"][g]:T["piece_node_off"][g + 1]].astype(np.int64)
+            assert np.array_equal(mem, np.nonzero(want_piece == c)[0])
+            assert np.array_equal(T["node_ppos"][q0 + mem], np.arange(mem.size))
+            # member edge lists: (other end's position, sqrt w) per half-edge,
+            # the same multiset as the block's observations touching the member
+            for i, l in enumerate(mem):
+                m_ = T["piece_node_off"][g] + i
+                ent = sorted(zip(T["edge_pos"][T["mem_rp"][m_]:T["mem_rp"][m_ + 1]].tolist(),
+                                 T["edge_sw"][T["mem_rp"][m_]:T["mem_rp"][m_ + 1]].tolist()))
+                want_ent = []
+                for e in np.nonzero((li == l) | (lj == l))[0]:
+                    other = lj[e] if li[e] == l else li[e]
+                    want_ent.append((int(np.nonzero(mem == other)[0][0]), float(R["obs_sw"][e0 + e])))
+                assert ent == sorted(want_ent)
+            if b % 7 and c % 3:            # a sample of the inverses
+                continue
+            n = mem.size
+            pos = {int(x): i for i, x in enumerate(mem)}
+            K = lam * np.eye(n)
+            for e in np.nonzero(want_piece[li] == c)[0]:
+                i, j = pos[int(li[e])], pos[int(lj[e])]
+                K[i, i] += w[e0 + e]; K[j, j] += w[e0 + e]; K[i, j] -= w[e0 + e]; K[j, i] -= w[e0 + e]
+            want = np.linalg.inv(K)
+            pk = T["inv"][T["piece_inv_off"][g]:T["piece_inv_off"][g + 1]].astype(np.float64)
+            got = pk.reshape(n, n)
+            assert np.array_equal(got, got.T)
+            worst = max(worst, float(np.abs(got - want).max() / np.abs(want).max()))
+    assert worst <= 2e-7, worst

@@ -310,7 +310,10 @@ int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
  * 1024 spent on the units of the CTA pass and of the last pass, [16..30] per
  * unit pass (one warp, CTA, last) five counters: SM cycles / 1024 in set-up,
  * the pieces' small inverses, the inverse of S, the refinement rounds, and
- * the units solved. */
+ * the units solved; [31..37] units the data-parallel unit solver handed to
+ * the CTA passes since the context was created, by reason: too many pieces,
+ * shared occurrences, shared nodes, shared nodes of one piece, a failed small
+ * inverse, a failed inverse of S, a full pool. */
 int spider_info(spider_ctx *ctx, int64_t *out, int32_t n);
 
 /* Sampler diagnostics of Sec. 3.6 at the current state, accumulated in FP64 on

@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspider.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["api.cu", "k_step.cu", "k_whiten.cu", "k_tt.cu", "k_mlp_tc.cu", "tt_noalloc.cu", "k_outlier.cu",
+CU_SOURCES = ["api.cu", "k_step.cu", "k_whiten.cu", "k_units.cu", "k_tt.cu", "k_mlp_tc.cu", "tt_noalloc.cu", "k_outlier.cu",
               "k_uq.cu"]
 CPP_SOURCES = ["prep.cpp", "pieces.cpp"]
 

@@ -42,8 +42,10 @@ struct spider_ctx {
   bool fast = false;               // tables built
   bool mb_full_sub = false;        // a sub-problem selects all its blocks in a minibatch
   int cc_grid = 0, clean_grid = 0;
-  int unit_grids[3] = {0, 0, 0};
+  int unit_grids[4] = {0, 0, 0, 0};   // [3]: SMs (the data-parallel unit solver)
   int64_t piece_bytes = 0;
+  cudaStream_t side = nullptr;     // second stream of the piece-inverse whitening
+  cudaEvent_t fork = nullptr, join = nullptr;
   int64_t n_samples = 0;           // samples written so far (ring of sample_cap)
   int64_t last_nb = 0;
   bool timing = false;
@@ -246,7 +248,8 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed, 
   if (timed) TRY(cudaEventRecord(c->ev[2], st));
   TRY(launch_resid(v, n_b, c->gu, st, timed ? &c->ev[3] : nullptr));
   if (fast) {
-    TRY(launch_whiten_fast(v, n_b, c->cfg.pcg_tol, c->cc_grid, c->unit_grids, c->clean_grid, st));
+    TRY(launch_whiten_fast(v, n_b, c->cfg.pcg_tol, c->cc_grid, c->unit_grids, c->clean_grid, st, c->side,
+                           c->fork, c->join));
     StepView vg = v;
     vg.gate = v.wfast + kWGeneral;
     TRY(launch_pcg(vg, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
@@ -385,6 +388,7 @@ int build_fast_whitening(spider_ctx* c, const Prep& P) {
   c->cc_grid = piece_cc_grid(c->num_sms);
   c->clean_grid = whiten_clean_grid(c->num_sms);
   if (c->cc_grid < 1 || whiten_units_grids(c->num_sms, c->unit_grids) < 1 || c->clean_grid < 1) return SPIDER_OK;
+  c->unit_grids[3] = c->num_sms;
   auto& L = c->allocs;
   StepView& v = c->v;
   cudaStream_t st = c->stream;
@@ -423,9 +427,27 @@ int build_fast_whitening(spider_ctx* c, const Prep& P) {
   ALF(unit_pblk, G);
   ALF(unit_defer, G);
   ALF(unit_defer2, G);
+  {
+    // the data-parallel unit solver: at most L_max occurrences per selected block
+    const size_t cap = (size_t)std::max<int64_t>(1, c->nb_mb) * (size_t)P.L_max;
+    v.u_cap = (int64_t)cap;
+    v.ginv_cap = int64_t(1) << 25;
+    v.sinv_cap = int64_t(1) << 24;
+    ALF(u_nocc, G); ALF(uocc_off, G + 1); ALF(u_ng, G); ALF(u_m, G);
+    ALF(u_gsz, G); ALF(u_goff, G + 1); ALF(u_ssz, G); ALF(u_soff, G + 1);
+    ALF(pu_base, G); ALF(pu_unit, G); ALF(pu_gb, G); ALF(pu_gn, G); ALF(pu_ginv, G);
+    ALF(o_g, cap); ALF(o_pe, cap); ALF(o_base, cap); ALF(o_u, cap); ALF(o_x, cap); ALF(o_unit, cap);
+    ALF(o_t, cap); ALF(o_i, cap);
+    ALF(o_uh, cap); ALF(o_ul, cap); ALF(o_zh, cap); ALF(o_zl, cap); ALF(o_f, cap); ALF(o_w, cap);
+    ALF(o_ph, cap); ALF(o_pl, cap);
+    ALF(sh_slot, cap); ALF(sh_sorted, cap); ALF(sh_tt, cap);
+    ALF(g_u, cap); ALF(g_beg, cap); ALF(g_cnt, cap);
+    ALF(g_uh, cap); ALF(g_ul, cap); ALF(g_zh, cap); ALF(g_zl, cap); ALF(g_f, cap); ALF(g_x, cap);
+    ALF(ginv_pool, (size_t)v.ginv_cap); ALF(sinv_pool, (size_t)v.sinv_cap);
+  }
   ALF(clean_list, G);
   ALF(clean_blk, G);
-  ALF(wfast, kWSlots + 64 + 16);
+  ALF(wfast, kWSlots + 64 + 32);
   ALF(wscratch, (size_t)c->unit_grids[2] * whiten_unit_scratch_floats());
 #undef UPF
 #undef ALF
@@ -450,6 +472,9 @@ int build_fast_whitening(spider_ctx* c, const Prep& P) {
     b0 = b1;
   }
   if ((e = cudaStreamSynchronize(st))) return cuda_fail(c, e, "upload sync");
+  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking))) return cuda_fail(c, e, "side stream");
+  if ((e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming))) return cuda_fail(c, e, "event");
+  if ((e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming))) return cuda_fail(c, e, "event");
   c->piece_bytes = bytes;
   c->fast = true;
   return SPIDER_OK;
@@ -470,6 +495,9 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
     last = c->err;
     g_static_err = last.c_str();
     free_all(c->allocs);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return code;
@@ -1177,16 +1205,17 @@ int spider_info(spider_ctx* c, int64_t* out, int32_t n) {
   int32_t cnt[kCntSlots] = {0};
   CK(c, cudaMemcpyAsync(cnt, c->v.counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
-  int32_t wf[kWSlots + 64 + 16] = {0};
+  int32_t wf[kWSlots + 64 + 32] = {0};
   if (c->fast) {
     CK(c, cudaMemcpyAsync(wf, c->v.wfast, sizeof(wf), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
   }
-  int64_t vals[31] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
+  int64_t vals[38] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
                       cnt[kCntComps], c->v.Q, c->fast ? 1 : 0, c->fast ? (c->mb_full_sub ? 0 : 1) : 0,
                       wf[kWUnits], wf[kWGeneral], wf[kWBigS], wf[kWCycSm], wf[kWCycBig]};
   for (int i = 0; i < 15; ++i) vals[16 + i] = wf[kWSlots + 64 + i];
-  for (int32_t i = 0; i < n && i < 31; ++i) out[i] = vals[i];
+  for (int i = 0; i < 7; ++i) vals[31 + i] = wf[kWSlots + 64 + 16 + i];
+  for (int32_t i = 0; i < n && i < 38; ++i) out[i] = vals[i];
   return SPIDER_OK;
 }
 
@@ -1240,6 +1269,12 @@ void spider_destroy(spider_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
   free_all(c->allocs);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

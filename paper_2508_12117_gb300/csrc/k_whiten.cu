@@ -873,7 +873,9 @@ using Smem1 = UnitSmem<32, 1024, 256, 64, 4096>;
 using Smem2 = UnitSmem<32, 1024, 256, 160, 8192>;
 
 cudaError_t configure_whiten_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_whiten_units<KW0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = configure_units_kernels();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_whiten_units<KW0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(Smem0));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_whiten_units<KW1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem1));
@@ -914,8 +916,11 @@ int piece_cc_grid(int num_sms) {
   return num_sms * (a < 2 ? a : 2);
 }
 
-cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[3],
-                               int clean_grid, cudaStream_t st) {
+// side, fork, join: a second stream and two events; the single pieces are
+// solved on the side stream while the units are solved on st
+cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[4],
+                               int clean_grid, cudaStream_t st, cudaStream_t side, cudaEvent_t fork,
+                               cudaEvent_t join) {
   if (!v.whiten) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(v.wfast, 0, kWSlots * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
@@ -932,10 +937,16 @@ cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc
   k_unit_ids<<<(unsigned)n_b, 256, 0, st>>>(v);
   k_unit_scan<<<1, 1024, 0, st>>>(v);
   k_unit_fill<<<(unsigned)n_b, 256, 0, st>>>(v);
-  k_whiten_clean<<<clean_grid, kCleanWarps * 32, 0, st>>>(v, tol);
-  k_whiten_units<KW0><<<grids[0], 32, sizeof(Smem0), st>>>(v, tol);
+  if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+  k_whiten_clean<<<clean_grid, kCleanWarps * 32, 0, side>>>(v, tol);
+  if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+  // units: data-parallel, then the CTA passes for the units it handed over
+  e = launch_units(v, tol, grids[3], st);
+  if (e != cudaSuccess) return e;
   k_whiten_units<KW1><<<grids[1], 256, sizeof(Smem1), st>>>(v, tol);
   k_whiten_units<KW2><<<grids[2], 256, sizeof(Smem2), st>>>(v, tol);
+  if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return e;
   k_whiten_stats<<<1, 32, 0, st>>>(v);
   return cudaGetLastError();
 }

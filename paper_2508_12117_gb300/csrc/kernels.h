@@ -45,8 +45,12 @@ cudaError_t configure_whiten_kernels();
 int whiten_units_grids(int num_sms, int grids[3]);
 int piece_cc_grid(int num_sms);
 int whiten_clean_grid(int num_sms);
-cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[3],
-                               int clean_grid, cudaStream_t st);
+// the units of a step, data-parallel (k_units.cu)
+cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st);
+cudaError_t configure_units_kernels();
+cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[4],
+                               int clean_grid, cudaStream_t st, cudaStream_t side, cudaEvent_t fork,
+                               cudaEvent_t join);
 // stage-1 outlier mask (k_outlier.cu)
 size_t outlier_scratch_bytes(int n_sub);
 cudaError_t launch_outlier(const StepView& v, int n_sub, float kmad, void* scratch, uint8_t* keep,

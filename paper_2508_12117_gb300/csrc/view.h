@@ -209,6 +209,19 @@ struct StepView {
   int32_t* clean_blk;             // [G]: their blocks
   int32_t* wfast;                 // [kWSlots] unit count, unit cursor, fallback flag, rounds
   float* wscratch;                // per CTA of the unit solver: S^-1 and the pieces' small inverses
+  // units solved data-parallel (k_units.cu): per unit [G (+1)], per unit piece
+  // entry [G], per occurrence slot [u_cap], pools of the small inverses
+  int32_t *u_nocc, *uocc_off, *u_ng, *u_m, *u_gsz, *u_goff, *u_ssz, *u_soff;
+  int32_t *pu_base, *pu_unit, *pu_gb, *pu_gn, *pu_ginv;
+  int32_t *o_g, *o_pe, *o_base, *o_u, *o_x, *o_unit, *o_t;
+  uint16_t* o_i;
+  float *o_uh, *o_ul, *o_zh, *o_zl, *o_f, *o_w, *o_ph, *o_pl;
+  int32_t *sh_slot, *sh_sorted;
+  float* sh_tt;
+  int32_t *g_u, *g_beg, *g_cnt;
+  float *g_uh, *g_ul, *g_zh, *g_zl, *g_f, *g_x;
+  float *ginv_pool, *sinv_pool;
+  int64_t u_cap, ginv_cap, sinv_cap;
   const int32_t* gate;            // non-null: the general solver runs only while *gate != 0
   float4* samples;
   float4* mom1;      // Adam first moment (M), null otherwise

@@ -318,7 +318,7 @@ def run_ours(args, rank, world):
     steps_s = replica_rate(world, K, ms_dev)
     state_bytes = cat.M * 32
     line = {
-        "metric": METRIC, "value": steps_s, "unit": "steps/s", "n_gpus": world, "steps": K,
+        "metric": METRIC if args.workload == 4 else f"SGLD steps/s ({cat.spec.name})", "value": steps_s, "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_dev / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": cat.spec.name, "events": cat.M, "stations": cat.S, "dd_obs": cat.N,
@@ -522,7 +522,8 @@ def run_reference(args, rank, world):
         return None
     cat, t_gen = build_workload(args.workload)
     base, secs = oracle_step(cat, 1_000_003 + 10_000)
-    return {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "steps/s",
+    metric = METRIC if args.workload == 4 else f"SGLD steps/s ({cat.spec.name})"
+    return {"impl": "reference", "metric": metric, "value": base["value"], "unit": "steps/s",
             "n_gpus": world, "steps": 1, "warmup": 0, "steps_requested": args.steps,
             "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",

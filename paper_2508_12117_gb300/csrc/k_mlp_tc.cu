@@ -13,27 +13,32 @@
 //
 // One CTA per SM, persistent over tiles; 19 warps:
 //   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one pair per
-//              lane); within every K-block of the next A operand, column group
+//              lane); within every K-block of the next operand, column group
 //              w / 4 takes a quarter of the K-block's columns, 16 at a time, so
-//              the K-blocks of A complete one after the other;
+//              the K-blocks of the operand complete one after the other;
 //   warp 16    producer: 1-D bulk async copies (cp.async.bulk) of pre-swizzled
-//              weight K-blocks (H rows x 64 BF16) into a two-stage ring;
+//              weight K-blocks (H rows x 128 bytes) into a four-stage ring;
 //   warp 18    geometry: loads the (event, station) geometry of the next tile
 //              into a shared-memory double buffer while the current tile runs;
-//   warp 17    MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M = 128, N = H,
-//              K = 16, A = activations (SW128 K-major, shared memory),
-//              B = weights (SW128 K-major), D = FP32 accumulator in TMEM.
+//   warp 17    MMA issuer: tcgen05.mma.cta_group::1, M = 128, N = H, A = the
+//              activations in TMEM, B = weights (SW128 K-major, shared memory),
+//              D = FP32 accumulator in TMEM.
 // TMEM (2H columns): two accumulators, [0, H) for products 0, 2, 4 and [H, 2H)
 // for products -1 (the first layer), 1, 3, 5 (forward W2, W3, W4, reverse
-// W4^T, W3^T, W2^T).  Product
-// l + 1 starts on K-block kb of its operand as soon as the epilogue of product l
-// has written that K-block (one barrier per K-block), into the accumulator the
-// epilogue is not reading; only its last K-block is left when the epilogue
-// finishes.  silu'(z1), silu'(z2), silu'(z3) (BF16) sit in three per-CTA slots
-// in global memory (each thread reads back only what it wrote; the stash loads
-// of a reverse layer are issued before its TMEM load).  At the end of a tile the
-// first 16 columns of [0, H) (last read by the product-4 epilogue) carry the
-// column groups' partial sums of tau and dtau/dx to the row's first group.
+// W4^T, W3^T, W2^T).  The epilogue of product l writes the operand of product
+// l + 1 over the accumulator it is reading, each thread into its own lane and
+// into columns it has already read: the values of the 16-column chunk at col
+// go, packed, to the first columns of their K-step (BF16: columns [col, col + 8)
+// hold K-step col / 16; E4M3: columns [32 s, 32 s + 8) hold K-step s), so
+// product l + 1 reads A from one accumulator and writes D into the other.  It
+// starts on K-block kb of its operand as soon as the epilogue of product l has
+// written that K-block (one barrier per K-block); only its last K-block is left
+// when the epilogue finishes.  The first layer's operand sits in columns
+// [16, 32) of [0, H).  silu'(z1), silu'(z2), silu'(z3) (BF16) sit in three
+// per-CTA slots in global memory (each thread reads back only what it wrote;
+// a reverse layer's first stash loads are issued before its product completes).
+// At the end of a tile the first 16 columns of [0, H) carry the column groups'
+// partial sums of tau and dtau/dx to the row's first group.
 // Four weight stages hold a whole layer at H = 256 (BF16), so the next layer's
 // weights are resident when its operand is ready.
 // Shared memory keeps W1 and the biases pre-halved (exact): the epilogue works
@@ -82,24 +87,28 @@ struct Cfg {
   static constexpr int EB = F8 ? 1 : 2;             // bytes per operand element
   static constexpr int KB = H * EB / 128;           // K-blocks (128-byte rows) per layer
   static constexpr int kChunk = H * 128;            // bytes of one weight K-block (H rows x 128 B)
-  static constexpr int kA = kRows * H * EB;         // activations, SW128 K-major
   static constexpr int kD = kRows * H * 2;          // one silu'(z) slot (BF16) in global memory
   static constexpr int kStash = 3 * kD;             // silu'(z1), silu'(z2), silu'(z3) per CTA
   static constexpr int kCols = H / kGroups;         // columns per epilogue thread
   static constexpr int kKbCols = H / KB;            // columns of one K-block of A
+  static constexpr int kKstep = kKbCols / 4;        // K of one MMA instruction (16 BF16 or 32 E4M3)
   static constexpr int kCpk = kKbCols / kGroups / kCc;   // 16-column chunks per thread and K-block
   static constexpr int kChunks = kCols / kCc;       // chunks per thread and layer
   static_assert(KB <= kMaxKb && kChunks == KB * kCpk && kCpk >= 1, "tile shape");
   static constexpr int kTmemCols = 2 * H;
   static constexpr int kChunksPerTile = 1 + 6 * KB;  // the first layer's image (one K-block), then 6 layers
   // shared-memory carve-up (offsets from a 1024-aligned base)
-  static constexpr int oA = 0;
-  static constexpr int oB = oA + kA;
+  static constexpr int oB = 0;
   static constexpr int oPar = oB + kStages * kChunk;      // W1 (6H), b1, b2, b3, b4, w5 (5H) floats
   static constexpr int oSc = oPar + 11 * H * 4;           // FP8: column scales of the 6 images (6H floats)
   static constexpr int oXch = oSc + (F8 ? 6 * H * 4 : 0); // FP8: row-bound exchange [2][kGroups][kRows] floats
   static constexpr int oGeo = oXch + (F8 ? 2 * kGroups * kRows * 4 : 0);   // pair geometry [2][15][kRows] floats
-  static constexpr int oBar = oGeo + 2 * 15 * kRows * 4;         // mbarriers
+  // silu'(z3) of the current tile (kD bytes) in shared memory when it fits
+  // (read by the first reverse layer, two products after it is written);
+  // otherwise it goes to the third global slot like silu'(z1), silu'(z2)
+  static constexpr int oD3 = oGeo + 2 * 15 * kRows * 4;
+  static constexpr bool kD3Shared = oD3 + kD + kBars * 8 + 16 + 1024 <= 232448;
+  static constexpr int oBar = oD3 + (kD3Shared ? kD : 0);         // mbarriers
   static constexpr int oMisc = oBar + kBars * 8;          // tmem base, abort flag
   static constexpr int kSmem = oMisc + 16 + 1024;         // + alignment slack
   static_assert(kSmem <= 232448, "shared memory per CTA");
@@ -122,6 +131,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
+// the same, letting the thread sleep (up to the hint, in ns) until the phase completes
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -139,7 +160,7 @@ __device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag
   if (mbar_test(b, parity)) return true;
   const uint64_t t0 = gtime();
   for (;;) {
-    if (mbar_test(b, parity)) return true;
+    if (mbar_test_sleep(b, parity)) return true;
     if (*abort_flag) return false;
     if (gtime() - t0 > kWaitNs) {
       *abort_flag = 1;
@@ -156,7 +177,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -176,21 +196,22 @@ __host__ __device__ constexpr uint32_t idesc_e4m3(int n) {
   return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 }
 
+// MMA with A read from tensor memory (lane = row, K packed along columns)
 template <bool F8>
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
   if constexpr (F8) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
   } else {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
   }
 }
@@ -202,6 +223,11 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
                "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
                : "memory");
 }
 __device__ __forceinline__ void tmem_ld16f(uint32_t taddr, float (&v)[16]) {
@@ -263,16 +289,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
 
-// byte offset of element (row r, k) in a 128-row SW128 K-major operand (K-blocks of 64)
-__device__ __forceinline__ uint32_t a_off(int r, int k) {
-  const int kb = k >> 6, j = (k >> 3) & 7;
-  return (uint32_t)(kb * (kRows * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + (k & 7) * 2);
-}
-// the same for 8-bit elements (K-blocks of 128)
-__device__ __forceinline__ uint32_t a_off8(int r, int k) {
-  const int kb = k >> 7, j = (k >> 4) & 7;
-  return (uint32_t)(kb * (kRows * 128) + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4) + (k & 15));
-}
 
 // four FP32 values -> four E4M3 bytes (round to nearest even, saturating), first value in the low byte
 __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
@@ -309,12 +325,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 uint8_t* __restrict__ stash) {
   using C = Cfg<H, F8>;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = sm + C::oA;
+  // 1024-byte aligned base by pointer arithmetic on the shared array itself, so
+  // that every access through it compiles to a shared-memory instruction (an
+  // integer round trip would leave generic addresses)
+  uint8_t* sm = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sB = sm + C::oB;
   // silu'(z1..3) of the current tile: this CTA's slots in global memory (each
   // thread reads back only what it wrote)
   uint8_t* sD = stash + (size_t)blockIdx.x * C::kStash;
+  uint8_t* sD3 = C::kD3Shared ? sm + C::oD3 : sD + 2 * (size_t)C::kD;   // the slot of silu'(z3)
   float* pW1 = reinterpret_cast<float*>(sm + C::oPar);
   float* pb1 = pW1 + 6 * H;
   float* pb = pb1 + H;       // b2, b3, b4
@@ -431,7 +450,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = F8 ? idesc_e4m3(H) : idesc_bf16(H);
       // descriptor of address a + d (d a multiple of 16, the sum below 2^18) = desc(a) + d / 16
-      const uint64_t adesc = sw128_desc(su32(sA)), bdesc = sw128_desc(su32(sB));
+      const uint64_t bdesc = sw128_desc(su32(sB));
       int64_t n = 0;        // weight chunks consumed
       uint32_t a_phase = 0;  // bit kb: phase of a_ready[kb]
       bool ok = true;
@@ -447,8 +466,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc_after();
           constexpr uint32_t idesc1 = idesc_bf16(H);
           const uint64_t bd = bdesc + (uint64_t)(s * (C::kChunk / 16));
-          umma<false>(tmem + (uint32_t)H, adesc, bd, idesc1, 0u);
-          umma<false>(tmem + (uint32_t)H, adesc + 2, bd + 2, idesc1, 1u);
+          // A: [x_hi, x_lo, x_hi, 0 ...] in columns [16, 32) of [0, H)
+          umma_ta<false>(tmem + (uint32_t)H, tmem + 16u, bd, idesc1, 0u);
+          umma_ta<false>(tmem + (uint32_t)H, tmem + 24u, bd + 2, idesc1, 1u);
           issued += 2;
           umma_commit(&empty[s]);
           ++n;
@@ -456,6 +476,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int layer = 0; layer < 6 && ok; ++layer) {
           const uint32_t d = tmem + (uint32_t)((layer & 1) * H);     // this product's accumulator
+          // its operand: written by the previous product's epilogue over that
+          // product's accumulator, K-step k (kKstep values) packed into the
+          // columns [k kKstep, k kKstep + 8)
+          const uint32_t a = tmem + (uint32_t)(((layer + 1) & 1) * H);
           for (int kb = 0; kb < C::KB; ++kb, ++n) {
             // K-block kb of the operand written (and the accumulator free: its last
             // reader, the epilogue two products back, finished before)
@@ -464,10 +488,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int s = (int)(n % kStages);
             if (!mbar_wait(&full[s], (uint32_t)((n / kStages) & 1), abort_flag, gerr)) { ok = false; break; }
             tc_after();
-            const uint64_t ad = adesc + (uint64_t)(kb * (kRows * 128 / 16));
+            const uint32_t ak = a + (uint32_t)(kb * C::kKbCols);
             const uint64_t bd = bdesc + (uint64_t)(s * (C::kChunk / 16));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) umma<F8>(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) ? 1u : 0u);
+            for (int k = 0; k < 4; ++k)
+              umma_ta<F8>(d, ak + (uint32_t)(k * C::kKstep), bd + 2 * k, idesc, (kb | k) ? 1u : 0u);
             issued += 4;
             umma_commit(&empty[s]);
           }
@@ -495,29 +520,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // this warp's part of K-block kb of the next operand is written (and its TMEM
     // reads before it are complete)
     auto a_done = [&](int kb) {
-      fence_async_smem();
+      tmem_wait_st();
       tc_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&a_ready[kb]);
     };
-    auto put_a = [&](int col, const float (&o)[kCc], float inv) {
+    // the next operand's values of columns col .. col + 15, packed into this
+    // row's lane of the accumulator just read (acc = its lane address): BF16
+    // pairs into columns [col, col + 8) (K-step col / 16); E4M3 quadruples into
+    // four of the eight columns of K-step col / 32, which starts at the first of
+    // this thread's two chunks of that K-step (both columns already read)
+    auto put_a = [&](uint32_t acc, int col, const float (&o)[kCc], float inv) {
       if constexpr (F8) {
         uint32_t hq[4];
 #pragma unroll
         for (int i = 0; i < kCc; i += 4)
           hq[i / 4] = pack_e4m3x4(o[i] * inv, o[i + 1] * inv, o[i + 2] * inv, o[i + 3] * inv);
-        *reinterpret_cast<uint4*>(sA + a_off8(r, col)) = make_uint4(hq[0], hq[1], hq[2], hq[3]);
+        tmem_st4(acc + (uint32_t)((col & ~31) + ((col & 16) >> 2)), hq);
       } else {
         uint32_t hp[8];
 #pragma unroll
         for (int i = 0; i < kCc; i += 2) hp[i / 2] = pack_bf16(o[i], o[i + 1]);
-        *reinterpret_cast<uint4*>(sA + a_off(r, col)) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-        *reinterpret_cast<uint4*>(sA + a_off(r, col + 8)) = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+        tmem_st8(acc + (uint32_t)col, hp);
       }
     };
     // silu'(z_q), q = 1, 2, 3, of columns col .. col + 15 into slot q
     auto put_d = [&](int q, int col, const uint32_t (&dp)[kCc / 2]) {
-      uint8_t* b = sD + (size_t)(q - 1) * C::kD;
+      uint8_t* b = q == 3 ? sD3 : sD + (size_t)(q - 1) * C::kD;
       *reinterpret_cast<uint4*>(b + d_off(r, col)) = make_uint4(dp[0], dp[1], dp[2], dp[3]);
       *reinterpret_cast<uint4*>(b + d_off(r, col + 8)) = make_uint4(dp[4], dp[5], dp[6], dp[7]);
     };
@@ -566,11 +595,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           q[i] = pack_bf16(a, b);
         }
-        *reinterpret_cast<uint4*>(sA + a_off(r, 8 * cg)) = make_uint4(q[0], q[1], q[2], q[3]);
+        // columns [16, 32) of [0, H): free since the previous tile's last product
+        tmem_st4(lane_addr + (uint32_t)(16 + 4 * cg), q);
         a_done(0);
       }
       // ---- the first layer (product -1), hidden layers and the reverse sweep
       for (int layer = -1; layer < 6; ++layer) {
+        // reverse layers: this thread's silu'(z_{6 - layer}) of the first kPre
+        // chunks is requested before the product completes (the slot was written
+        // two to four products earlier, so the loads' latency hides behind the
+        // MMA); chunk j + kPre is requested while chunk j is processed
+        constexpr int kPre = C::kChunks < 2 ? C::kChunks : 2;
+        const uint8_t* dsl = layer == 3 ? sD3 : sD + (size_t)(layer >= 3 ? 5 - layer : 0) * C::kD;
+        uint4 dsv[2 * kPre];
+        if (layer >= 3) {
+#pragma unroll
+          for (int j = 0; j < kPre; ++j) {
+            dsv[2 * j] = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j)));
+            dsv[2 * j + 1] = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j) + 8));
+          }
+        }
         const bool got = mbar_wait(acc_ready, acc_phase, abort_flag, gerr);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
         acc_phase ^= 1;
@@ -609,34 +653,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             sa_next = s4;
           }
         }
-        // reverse layers: silu'(z_{6 - layer}) of chunk j + 1 is loaded while chunk j
-        // is processed (BF16 with four or more chunks per thread; else chunk by chunk)
-        constexpr bool kAhead = !F8 && C::kChunks >= 4;
-        const uint8_t* dsl = sD + (size_t)(layer >= 3 ? 5 - layer : 0) * C::kD;
-        uint4 dn0 = make_uint4(0, 0, 0, 0), dn1 = dn0;
-        if (kAhead && layer >= 3) {
-          dn0 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(0)));
-          dn1 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(0) + 8));
-        }
-#pragma unroll 1
+        // chunk j + 1 is read from TMEM while chunk j is processed (two register
+        // buffers; tcgen05.wait::ld at the end of chunk j waits for that one read)
+        float vb[2][kCc];
+        tmem_ld16f(acc + ccol(0), vb[0]);
+        tmem_wait_ld();
+#pragma unroll
         for (int j = 0; j < C::kChunks; ++j) {
           const int col = ccol(j);
-          uint32_t dd[kCc / 2];
-          if (layer >= 3) {
-            if (!kAhead) {
-              dn0 = *reinterpret_cast<const uint4*>(dsl + d_off(r, col));
-              dn1 = *reinterpret_cast<const uint4*>(dsl + d_off(r, col + 8));
-            }
-            dd[0] = dn0.x; dd[1] = dn0.y; dd[2] = dn0.z; dd[3] = dn0.w;
-            dd[4] = dn1.x; dd[5] = dn1.y; dd[6] = dn1.z; dd[7] = dn1.w;
-            if (kAhead && j + 1 < C::kChunks) {
-              dn0 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j + 1)));
-              dn1 = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j + 1) + 8));
-            }
-          }
-          float v[kCc];
-          tmem_ld16f(acc + col, v);
-          tmem_wait_ld();
+          if (j + 1 < C::kChunks) tmem_ld16f(acc + ccol(j + 1), vb[(j + 1) & 1]);
+          float* v = vb[j & 1];
           if constexpr (F8) {
 #pragma unroll
             for (int i = 0; i < kCc; ++i) v[i] *= dq(col + i);
@@ -647,28 +673,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float* bias = pb + layer * H;
             uint32_t dp[kCc / 2];
 #pragma unroll
-            for (int i = 0; i < kCc; i += 2) {
-              uint64_t hh, dd2;
-              silu_half(f2fma(f2pack(v[i], v[i + 1]), kHalf2, *reinterpret_cast<const uint64_t*>(bias + col + i)), hh,
-                        dd2);
-              float h0, d0, h1, d1;
-              f2unpack(hh, h0, h1);
-              if (layer == 2) {
-                const uint64_t w = *reinterpret_cast<const uint64_t*>(pw5 + col + i);
-                float w0, w1;
-                f2unpack(w, w0, w1);
-                tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
-                f2unpack(f2mul(w, dd2), o[i], o[i + 1]);          // delta4
-              } else {
-                f2unpack(dd2, d0, d1);
-                o[i] = h0;
-                o[i + 1] = h1;
-                dp[i / 2] = pack_bf16(d0, d1);
+            for (int i = 0; i < kCc; i += 4) {
+              const float4 b4 = *reinterpret_cast<const float4*>(bias + col + i);
+              uint64_t hh[2], dd2[2];
+              silu_half(f2fma(f2pack(v[i], v[i + 1]), kHalf2, f2pack(b4.x, b4.y)), hh[0], dd2[0]);
+              silu_half(f2fma(f2pack(v[i + 2], v[i + 3]), kHalf2, f2pack(b4.z, b4.w)), hh[1], dd2[1]);
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                const int ii = i + 2 * q;
+                float h0, h1;
+                f2unpack(hh[q], h0, h1);
+                if (layer == 2) {
+                  const uint64_t w = *reinterpret_cast<const uint64_t*>(pw5 + col + ii);
+                  float w0, w1;
+                  f2unpack(w, w0, w1);
+                  tpart = fmaf(w0, h0, fmaf(w1, h1, tpart));
+                  f2unpack(f2mul(w, dd2[q]), o[ii], o[ii + 1]);          // delta4
+                } else {
+                  float d0, d1;
+                  f2unpack(dd2[q], d0, d1);
+                  o[ii] = h0;
+                  o[ii + 1] = h1;
+                  dp[ii / 2] = pack_bf16(d0, d1);
+                }
               }
             }
             if (layer < 2) put_d(layer + 2, col, dp);  // silu'(z1), silu'(z2), silu'(z3)
           } else {
             // reverse sweep: delta_{l-1} = acc * silu'(z_{l-1})
+            const int sl = j % kPre;
+            const uint32_t dd[8] = {dsv[2 * sl].x, dsv[2 * sl].y, dsv[2 * sl].z, dsv[2 * sl].w,
+                                    dsv[2 * sl + 1].x, dsv[2 * sl + 1].y, dsv[2 * sl + 1].z, dsv[2 * sl + 1].w};
+            if (j + kPre < C::kChunks) {
+              dsv[2 * sl] = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j + kPre)));
+              dsv[2 * sl + 1] = *reinterpret_cast<const uint4*>(dsl + d_off(r, ccol(j + kPre) + 8));
+            }
 #pragma unroll
             for (int i = 0; i < kCc; i += 2)
               f2unpack(f2mul(f2pack(v[i], v[i + 1]), f2pack(bf16_lo(dd[i / 2]), bf16_hi(dd[i / 2]))), o[i],
@@ -692,9 +731,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           }
           if (layer < 5) {
-            put_a(col, o, inv);
+            put_a(acc, col, o, inv);
             if ((j + 1) % C::kCpk == 0) a_done(j / C::kCpk);
           }
+          if (j + 1 < C::kChunks) tmem_wait_ld();
         }
         if (!ok) break;
         sa = sa_next;

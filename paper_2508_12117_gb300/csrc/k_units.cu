@@ -27,11 +27,12 @@ namespace spider {
 namespace {
 
 constexpr int kUMaxPieces = 32;    // pieces of a unit
-constexpr int kUMaxShared = 512;   // shared occurrences of a unit
-constexpr int kUMaxGamma = 160;    // shared nodes of a unit
+constexpr int kUMaxShared = 1024;  // shared occurrences of a unit
+constexpr int kUMaxGamma = 192;    // shared nodes of a unit
 constexpr int kUWarpGamma = 64;    // S^-1 by one warp up to this size, by a CTA above
-constexpr int kUMaxGp = 64;        // shared nodes of one piece
+constexpr int kUMaxGp = 96;        // shared nodes of one piece
 constexpr int kUWarps = 8;         // warps per CTA of the per-unit kernels
+constexpr int kUOccWarps = 4;      // warps per CTA of k_u_occ (a sort buffer of kUMaxShared keys each)
 constexpr int kUTh = 256;          // threads per CTA of the per-occurrence kernels
 
 __device__ __forceinline__ int gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
@@ -159,8 +160,8 @@ __global__ void k_u_scan(const int32_t* __restrict__ cnt, const int32_t* n_dev, 
 }
 
 // occurrence tables, shared lists and shared nodes (one warp per unit)
-__global__ void __launch_bounds__(kUWarps * 32) k_u_occ(StepView v) {
-  __shared__ unsigned long long keys[kUWarps][kUMaxShared];
+__global__ void __launch_bounds__(kUOccWarps * 32) k_u_occ(StepView v) {
+  __shared__ unsigned long long keys[kUOccWarps][kUMaxShared];
   if (aborted(v)) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int32_t nu = v.wfast[kWUnits];
@@ -300,8 +301,8 @@ __global__ void __launch_bounds__(kUWarps * 32) k_u_occ(StepView v) {
 }
 
 // (A_p[G,G])^-1 of every piece of every valid unit (one warp per piece)
-// pieces with MINN < g_p <= MAXN shared nodes (two launches: small ones with
-// little shared memory per warp, hence many warps per SM, then the rest)
+// pieces with MINN < g_p <= MAXN shared nodes (one launch per size class: the
+// small ones with little shared memory per warp, hence many warps per SM)
 template <int MINN, int MAXN, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_u_ginv(StepView v) {
   __shared__ float Ms[WARPS][MAXN * MAXN];
@@ -712,11 +713,12 @@ cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t
   int32_t* n_units = v.wfast + kWUnits;
   k_u_prep<<<gw, kUWarps * 32, 0, st>>>(v);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_nocc, n_units, v.uocc_off, v.u_cap, v.wfast);
-  k_u_occ<<<gw, kUWarps * 32, 0, st>>>(v);
+  k_u_occ<<<gw * (kUWarps / kUOccWarps), kUOccWarps * 32, 0, st>>>(v);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_gsz, n_units, v.u_goff, v.ginv_cap, v.wfast);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_ssz, n_units, v.u_soff, v.sinv_cap, v.wfast);
   k_u_ginv<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
   k_u_ginv<32, 64, 2><<<num_sms * 7, 64, 0, st>>>(v);
+  k_u_ginv<64, 96, 1><<<num_sms * 2, 32, 0, st>>>(v);
   k_u_sinv<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
   k_u_sinv<32, 64, 2><<<num_sms * 7, 64, 0, st>>>(v);
   k_u_sinv_big<<<num_sms, 256, kUMaxGamma * kUMaxGamma * sizeof(float), st>>>(v);

@@ -92,7 +92,10 @@ def spec(wid: int) -> Spec:
                     medium="homogeneous", noise="normal", noise_s=0.01,
                     forward="homogeneous", hyper=h)
     if wid == 2:
-        h = Hyper(sigma=0.005, eps=_eps_for(0.03, 10, 1.0), batch_n=0)
+        # full batch: an event's ~400 dd observations all act in every step, so
+        # the curvature per origin time is ~20x that of the minibatch workloads
+        # (a step of 0.2 kappa^2 / 10 grows the error ~3x per step)
+        h = Hyper(sigma=0.005, eps=_eps_for(0.03, 200, 1.0), batch_n=0)
         return Spec("mlp128-10kev-2Mdd", 2, 10_000, 50, 20, 10, "faults", n_faults=5,
                     region_km=20.0, medium="gradient", noise="normal", noise_s=0.005,
                     forward="mlp", hidden=128, hyper=h)

@@ -248,7 +248,7 @@ def run_ours(args, rank, world):
     time.sleep(0.5)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stage = np.zeros(5)
-    kern = {}
+    kern, wphase = {}, {}
     pairs = nobs = iters = touched = 0
     torch.cuda.synchronize()
     ev0.record(stream)
@@ -256,9 +256,12 @@ def run_ours(args, rank, world):
         ctx.spider_sgld_step(eps, seed0 + args.warmup + s)
         tm = ctx.spider_last_timing()      # waits for the step's events
         kt, te = ctx.spider_last_kernel_timing()
+        wt = ctx.spider_last_whiten_timing()
         stage += np.array(tm["ms"])
         for k_, v_ in kt.items():
             kern[k_] = kern.get(k_, 0.0) + v_
+        for k_, v_ in wt.items():
+            wphase[k_] = wphase.get(k_, 0.0) + v_
         pairs += tm["pairs"]; nobs += tm["n_obs"]; iters += tm["pcg_iters"]; touched += te
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -335,6 +338,7 @@ def run_ours(args, rank, world):
                               "residual_whitening": stage[2] / K, "scatter_update": stage[3] / K,
                               "with_host_reads_ms_per_step": ms_total / K},
         "kernel_ms_per_step": kms,
+        "whitening_phases_ms_per_step": {k_: v_ / K for k_, v_ in wphase.items()},
         "roofline": roof,
         "roofline_hbm": hbm,
         "e2e": {"value": replica_rate(world, K, e2e_ms), "unit": "steps/s", "h2d_bytes_per_step": 0,

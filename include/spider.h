@@ -279,6 +279,16 @@ int spider_last_timing(spider_ctx *ctx, float out_ms[5], int64_t *pairs,
  * *touched_events: events with at least one pair in the minibatch. */
 int spider_last_kernel_timing(spider_ctx *ctx, float out_ms[10], int64_t *touched_events);
 
+/* Phases of the whitening solve of the last timed evaluation, when it took
+ * the piece-inverse path (all zero otherwise; synchronous): [0] labelling the
+ * selected pieces and grouping them into units, [1] the units' set-up (their
+ * shared nodes, the pieces' (A_p[G,G])^-1 and S^-1), [2] the units' Schur
+ * rounds and convergence check, [3] the CTA passes for units beyond the
+ * data-parallel limits, [4] waiting for the clean-piece solver on its side
+ * stream, [5] the general component solver (a no-op unless a unit exceeded
+ * every limit).  Device ms from CUDA events. */
+int spider_last_whiten_timing(spider_ctx *ctx, float out_ms[6]);
+
 /* Debug views of the last evaluation (synchronous):
  * spider_debug_blocks: selected block ids in selection order (int64, cap);
  * spider_debug_obs: for every observation of the last minibatch, its caller
@@ -293,8 +303,10 @@ int spider_debug_obs(spider_ctx *ctx, int64_t *idx_out, float *r_out, float *q_o
  * knobs[1] of the per-component CTA solver (1..4), knobs[2] CTAs per SM of
  * the FP32 MLP kernel (1..2), knobs[3] 1 (default): minibatch steps whiten
  * through the precomputed inverses of the block-local components when they
- * were built, 0: always through the general component solver.  Invalidates
- * the captured step graph. */
+ * were built, 0: always through the general component solver; knobs[4]
+ * (0..4, default 2) the share, in quarters, of the persistent grid the
+ * clean-piece solver takes on its side stream while the units are solved
+ * (0: it runs after them on the context's stream).  Invalidates the captured step graph. */
 int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
 
 /* Facts about a context (synchronous), out[0..n): [0] sub-problems,

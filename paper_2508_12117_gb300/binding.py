@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "spider_set_timing": (C.c_int, [vp, C.c_int]),
         "spider_set_wait_limit_ns": (C.c_int, [vp, u64]),
         "spider_last_kernel_timing": (C.c_int, [vp, pf, pi64]),
+        "spider_last_whiten_timing": (C.c_int, [vp, pf]),
         "spider_last_timing": (C.c_int, [vp, pf, pi64, pi64, C.POINTER(i32)]),
         "spider_debug_blocks": (C.c_int, [vp, pi64, i64, pi64]),
         "spider_debug_obs": (C.c_int, [vp, pi64, pf, pf, i64, pi64]),
@@ -356,6 +357,14 @@ class Context:
         names = ["select_pairs", "travel_time", "k_resid", "k_merge_rhs", "whitening", "k_final",
                  "k_merge_s", "centroid", "k_event", "logpost"]
         return dict(zip(names, list(ms))), ev.value
+
+    def spider_last_whiten_timing(self):
+        """Device ms of the whitening phases of the last timed evaluation (see
+        include/spider.h); zeros unless it took the piece-inverse path."""
+        ms = (C.c_float * 6)()
+        _check(load_library().spider_last_whiten_timing(self.h, ms), self.h)
+        names = ["pieces", "unit_setup", "unit_rounds", "cta_passes", "clean_wait", "general"]
+        return dict(zip(names, list(ms)))
 
     def spider_set_wait_limit_ns(self, limit_ns: int):
         _check(load_library().spider_set_wait_limit_ns(self.h, int(limit_ns)), self.h)

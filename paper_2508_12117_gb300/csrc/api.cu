@@ -37,7 +37,7 @@ struct spider_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_ok = true;
   bool use_graph = true;
-  int32_t knobs[4] = {2, 1, 2, 1};   // see spider_set_tuning
+  int32_t knobs[5] = {2, 1, 2, 1, 2};   // see spider_set_tuning
   // whitening through precomputed piece inverses (minibatch steps)
   bool fast = false;               // tables built
   bool mb_full_sub = false;        // a sub-problem selects all its blocks in a minibatch
@@ -58,6 +58,8 @@ struct spider_ctx {
   // centroid, k_event, end
   static constexpr int kEv = 11;
   cudaEvent_t ev[kEv] = {};
+  cudaEvent_t wev[5] = {};          // whitening phases (timed evaluations of the piece path)
+  bool have_wtiming = false;
   float last_ms[5] = {0, 0, 0, 0, 0};
   bool have_timing = false;
 };
@@ -249,7 +251,7 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed, 
   TRY(launch_resid(v, n_b, c->gu, st, timed ? &c->ev[3] : nullptr));
   if (fast) {
     TRY(launch_whiten_fast(v, n_b, c->cfg.pcg_tol, c->cc_grid, c->unit_grids, c->clean_grid, st, c->side,
-                           c->fork, c->join));
+                           c->fork, c->join, timed ? c->wev : nullptr, c->knobs[4]));
     StepView vg = v;
     vg.gate = v.wfast + kWGeneral;
     TRY(launch_pcg(vg, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
@@ -323,6 +325,7 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
   }
   c->last_nb = n_b;
   c->have_timing = c->timing;
+  c->have_wtiming = c->timing && fast;
   return SPIDER_OK;
 }
 
@@ -495,6 +498,10 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
     last = c->err;
     g_static_err = last.c_str();
     free_all(c->allocs);
+    for (auto& ev : c->ev)
+      if (ev) cudaEventDestroy(ev);
+    for (auto& ev : c->wev)
+      if (ev) cudaEventDestroy(ev);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
@@ -762,6 +769,8 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
   c->th0 = std::move(P.th0);
   for (int i = 0; i < spider_ctx::kEv; ++i)
     if ((e = cudaEventCreate(&c->ev[i]))) return bail(cuda_fail(c, e, "event"));
+  for (int i = 0; i < 5; ++i)
+    if ((e = cudaEventCreate(&c->wev[i]))) return bail(cuda_fail(c, e, "event"));
   if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "create sync"));
   *out = c;
   return SPIDER_OK;
@@ -1145,6 +1154,17 @@ int spider_last_kernel_timing(spider_ctx* c, float out_ms[10], int64_t* touched_
   return SPIDER_OK;
 }
 
+int spider_last_whiten_timing(spider_ctx* c, float out_ms[6]) {
+  if (!c || !out_ms) return SPIDER_E_INVAL;
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 6; ++i) out_ms[i] = 0.f;
+  if (!c->have_wtiming) return SPIDER_OK;
+  const cudaEvent_t a[6] = {c->ev[4], c->wev[0], c->wev[1], c->wev[2], c->wev[3], c->wev[4]};
+  const cudaEvent_t b[6] = {c->wev[0], c->wev[1], c->wev[2], c->wev[3], c->wev[4], c->ev[5]};
+  for (int i = 0; i < 6; ++i) CK(c, cudaEventElapsedTime(&out_ms[i], a[i], b[i]));
+  return SPIDER_OK;
+}
+
 int spider_debug_blocks(spider_ctx* c, int64_t* out, int64_t cap, int64_t* n) {
   if (!c || !n || (cap > 0 && !out)) return SPIDER_E_INVAL;
   std::vector<int32_t> s(c->last_nb);
@@ -1185,14 +1205,14 @@ int spider_debug_obs(spider_ctx* c, int64_t* idx_out, float* r_out, float* q_out
 
 int spider_set_tuning(spider_ctx* c, const int32_t* knobs, int32_t n) {
   if (!c || (n > 0 && !knobs)) return SPIDER_E_INVAL;
-  const int32_t lo[4] = {1, 1, 1, 0}, hi[4] = {8, 4, 2, 1};
-  for (int32_t i = 0; i < n && i < 4; ++i)
+  const int32_t lo[5] = {1, 1, 1, 0, 0}, hi[5] = {8, 4, 2, 1, 4};
+  for (int32_t i = 0; i < n && i < 5; ++i)
     if (knobs[i] < lo[i] || knobs[i] > hi[i]) {
       c->err = "tuning knob out of range";
       return SPIDER_E_INVAL;
     }
   CK(c, cudaStreamSynchronize(c->stream));
-  for (int32_t i = 0; i < n && i < 4; ++i) c->knobs[i] = knobs[i];
+  for (int32_t i = 0; i < n && i < 5; ++i) c->knobs[i] = knobs[i];
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
@@ -1266,6 +1286,8 @@ void spider_destroy(spider_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->wev)
     if (e) cudaEventDestroy(e);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);

@@ -8,7 +8,9 @@
 // in slot order and sorted by pair, its shared nodes), each shorter than it.
 // Set-up (once per step): sorted pieces and member counts (one warp per unit);
 // occurrence tables, shared lists and shared nodes (one warp per unit); the
-// pieces' (A_p[G,G])^-1 (one warp per piece); S^-1 (one warp per unit).
+// pieces' (A_p[G,G])^-1 and the units' S^-1 by Gauss-Jordan (a warp per matrix
+// in shared memory up to 32 nodes, a CTA per matrix in registers up to 64 (96
+// for the pieces), S^-1 above 64 nodes in shared memory by one CTA per unit).
 // Each refinement round: residual (one thread per occurrence, then per shared
 // node), w = A_p[:, I] f_I (one thread per occurrence), the small dense Schur
 // solve (one warp per unit), the update of z (one thread per occurrence).
@@ -94,6 +96,68 @@ __device__ bool warp_gj(float* M, int n, int lane) {
     __syncwarp();
   }
   return true;
+}
+
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (NT == 32) __syncwarp(); else __syncthreads();
+}
+
+// Gauss-Jordan inverse of an SPD n x n matrix (n <= NP, padded with the
+// identity) held in registers by a group of NT threads: thread t owns column
+// j = t % NP, rows RB (t / NP) .. RB (t / NP) + RB - 1 (NT RB = NP^2).  At pivot
+// k the owners of column k and of row k publish them in shared memory (two
+// alternating buffers of NP floats each, so one barrier per pivot suffices)
+// and every thread updates its strip with
+//   m_ij -= m_ik m_kj / p (i, j != k),  m_kj /= p,  m_ik = -m_ik / p,  m_kk = 1 / p.
+// Shared-memory traffic per pivot is the two published vectors, not the matrix.
+// False when a pivot is not positive (every thread of the group sees the same
+// pivots, so the result is uniform).
+template <int NP, int RB, int NT>
+__device__ __forceinline__ bool strip_gj(float (&m)[RB], int t, float* ck2, float* rk2) {
+  static_assert(NP * NP == NT * RB, "strip shape");
+  const int j = t % NP, rb = t / NP;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    float* ck = ck2 + (k & 1) * NP;
+    float* rk = rk2 + (k & 1) * NP;
+    if (j == k) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) ck[rb * RB + r] = m[r];
+    }
+    if (rb == k / RB) rk[j] = m[k % RB];
+    group_sync<NT>();
+    const float p = ck[k];
+    if (!(p > 0.f)) ok = false;
+    const float ip = 1.f / p;
+    const float mkj = rk[j] * ip;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) m[r] = fmaf(-ck[rb * RB + r], mkj, m[r]);
+    if (rb == k / RB) m[k % RB] = mkj;
+    if (j == k) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) m[r] = -ck[rb * RB + r] * ip;
+      if (rb == k / RB) m[k % RB] = ip;
+    }
+  }
+  group_sync<NT>();
+  return ok;
+}
+
+// a value every thread of the group reads the same (lane 0 / thread 0 reads it)
+template <int NT>
+__device__ __forceinline__ int group_read(const int32_t* p, int t, int* slot) {
+  if constexpr (NT == 32) {
+    int x = 0;
+    if (t == 0) x = *((volatile const int32_t*)p);
+    return __shfl_sync(0xffffffffu, x, 0);
+  } else {
+    __syncthreads();
+    if (t == 0) *slot = *((volatile const int32_t*)p);
+    __syncthreads();
+    return *slot;
+  }
 }
 
 // ------------------------------------------------------------------ set-up
@@ -300,12 +364,15 @@ __global__ void __launch_bounds__(kUOccWarps * 32) k_u_occ(StepView v) {
   }
 }
 
+// the small classes by one warp per matrix in shared memory (many warps per
+// SM; the strip form below pays for its registers in occupancy there):
 // (A_p[G,G])^-1 of every piece of every valid unit (one warp per piece)
 // pieces with MINN < g_p <= MAXN shared nodes (one launch per size class: the
 // small ones with little shared memory per warp, hence many warps per SM)
 template <int MINN, int MAXN, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_u_ginv(StepView v) {
+__global__ void __launch_bounds__(WARPS * 32) k_u_ginv_w(StepView v) {
   __shared__ float Ms[WARPS][MAXN * MAXN];
+  __shared__ int Is[WARPS][MAXN];     // the shared members' rows in the piece inverse
   if (aborted(v)) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int32_t npe = v.unit_off[v.wfast[kWUnits]];
@@ -324,9 +391,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_u_ginv(StepView v) {
       if (lane == 0) give_up_unit(v, u, 6);
       continue;
     }
+    int* I = Is[w];
+    for (int c = lane; c < gn; c += 32) I[c] = v.o_i[v.sh_slot[O + gb + c]];
+    __syncwarp();
     for (int c = lane; c < gn; c += 32) {
-      const int ic = v.o_i[v.sh_slot[O + gb + c]];
-      for (int a = 0; a < gn; ++a) M[a * gn + c] = __ldg(A + (size_t)v.o_i[v.sh_slot[O + gb + a]] * n + ic);
+      const float* Ac = A + I[c];
+#pragma unroll 8
+      for (int a = 0; a < gn; ++a) M[a * gn + c] = __ldg(Ac + (size_t)I[a] * n);
     }
     __syncwarp();
     const bool ok = warp_gj(M, gn, lane);
@@ -342,8 +413,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_u_ginv(StepView v) {
 
 // S = sum_p R_p^T (A_p[G,G])^-1 R_p - lambda diag(c - 1), then S^-1 (one warp per unit)
 template <int MINN, int MAXN, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_u_sinv(StepView v) {
+__global__ void __launch_bounds__(WARPS * 32) k_u_sinv_w(StepView v) {
   __shared__ float Ss[WARPS][MAXN * MAXN];
+  __shared__ int Xs[WARPS][kUMaxGp];   // a piece's shared members as indices into S
   if (aborted(v)) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int32_t nu = v.wfast[kWUnits];
@@ -364,9 +436,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_u_sinv(StepView v) {
       const int gn = v.pu_gn[e0 + p], gb = v.pu_gb[e0 + p];
       if (gn == 0) continue;
       const float* G = v.ginv_pool + v.u_goff[u] + v.pu_ginv[e0 + p];
+      int* X = Xs[w];
+      for (int c = lane; c < gn; c += 32) X[c] = v.o_x[v.sh_slot[O + gb + c]] - O;
+      __syncwarp();
       for (int c = lane; c < gn; c += 32) {
-        const int xc = v.o_x[v.sh_slot[O + gb + c]] - O;
-        for (int a = 0; a < gn; ++a) S[(v.o_x[v.sh_slot[O + gb + a]] - O) * ng + xc] += G[a * gn + c];
+        const int xc = X[c];
+#pragma unroll 4
+        for (int a = 0; a < gn; ++a) S[X[a] * ng + xc] += G[a * gn + c];
       }
       __syncwarp();
     }
@@ -382,11 +458,130 @@ __global__ void __launch_bounds__(WARPS * 32) k_u_sinv(StepView v) {
   }
 }
 
+// (A_p[G,G])^-1 of every piece of every valid unit whose number of shared
+// members g_p lies in (MINN, MAXN]: one group of NT threads per piece (strip_gj;
+// GROUPS groups per CTA), the matrix gathered straight into registers
+template <int MINN, int MAXN, int NP, int RB, int NT, int GROUPS>
+__global__ void __launch_bounds__(NT * GROUPS) k_u_ginv(StepView v) {
+  static_assert(MAXN <= NP && (NT == 32 || GROUPS == 1), "group shape");
+  __shared__ float Cs[GROUPS][2 * NP], Rs[GROUPS][2 * NP];
+  __shared__ int Is[GROUPS][NP];      // the shared members' rows in the piece inverse
+  __shared__ int flag[GROUPS];
+  if (aborted_cta(v)) return;
+  const int grp = threadIdx.x / NT, t = threadIdx.x % NT;
+  const int j = t % NP, rb = t / NP;
+  const int32_t npe = v.unit_off[v.wfast[kWUnits]];
+  for (int32_t pe = blockIdx.x * GROUPS + grp; pe < npe; pe += gridDim.x * GROUPS) {
+    const int32_t u = v.pu_unit[pe];
+    const int gn = v.pu_gn[pe];
+    if (gn <= MINN || gn > MAXN) continue;
+    if (group_read<NT>(&v.u_ng[u], t, &flag[grp]) < 0) continue;
+    const int32_t O = v.uocc_off[u];
+    const int32_t g = v.unit_pieces[pe];
+    const int n = v.piece_node_off[g + 1] - v.piece_node_off[g];
+    const float* A = v.piece_inv + v.piece_inv_off[g];
+    const int gb = v.pu_gb[pe];
+    const int64_t dst_off = (int64_t)v.u_goff[u] + v.pu_ginv[pe];
+    if (dst_off + (int64_t)gn * gn > v.ginv_cap) {
+      if (t == 0) give_up_unit(v, u, 6);
+      continue;
+    }
+    // the index chain (slot -> occurrence -> member) once per member
+    int* I = Is[grp];
+    for (int c = t; c < gn; c += NT) I[c] = v.o_i[v.sh_slot[O + gb + c]];
+    group_sync<NT>();
+    float m[RB];
+    const int ij = j < gn ? I[j] : 0;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int i = rb * RB + r;
+      m[r] = (i < gn && j < gn) ? __ldg(A + (size_t)I[i] * n + ij) : (i == j ? 1.f : 0.f);
+    }
+    if (!strip_gj<NP, RB, NT>(m, t, Cs[grp], Rs[grp])) {
+      if (t == 0) give_up_unit(v, u, 4);
+      continue;
+    }
+    float* dst = v.ginv_pool + dst_off;
+    if (j < gn) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int i = rb * RB + r;
+        if (i < gn) dst[i * gn + j] = m[r];
+      }
+    }
+  }
+}
+
+// S = sum_p R_p^T (A_p[G,G])^-1 R_p - lambda diag(c - 1) assembled in shared
+// memory (pieces in order: a fixed summation order), then S^-1 by strip_gj in
+// registers; units with MINN < ng <= MAXN, one group of NT threads per unit
+template <int MINN, int MAXN, int NP, int RB, int NT, int GROUPS>
+__global__ void __launch_bounds__(NT * GROUPS) k_u_sinv(StepView v) {
+  static_assert(MAXN <= NP && (NT == 32 || GROUPS == 1), "group shape");
+  __shared__ float Ss[GROUPS][MAXN * MAXN];
+  __shared__ float Cs[GROUPS][2 * NP], Rs[GROUPS][2 * NP];
+  __shared__ int Xs[GROUPS][kUMaxGp];   // a piece's shared members as indices into S
+  __shared__ int flag[GROUPS];
+  if (aborted_cta(v)) return;
+  const int grp = threadIdx.x / NT, t = threadIdx.x % NT;
+  const int j = t % NP, rb = t / NP;
+  const int32_t nu = v.wfast[kWUnits];
+  const float lam = v.lam;
+  for (int32_t u = blockIdx.x * GROUPS + grp; u < nu; u += gridDim.x * GROUPS) {
+    const int ng = group_read<NT>(&v.u_ng[u], t, &flag[grp]);
+    if (ng <= MINN || ng > MAXN) continue;
+    const int32_t O = v.uocc_off[u], e0 = v.unit_off[u];
+    const int k = v.unit_off[u + 1] - e0;
+    if ((int64_t)v.u_soff[u] + (int64_t)ng * ng > v.sinv_cap || (int64_t)v.u_goff[nu] > v.ginv_cap) {
+      if (t == 0) give_up_unit(v, u, 6);
+      continue;
+    }
+    float* S = Ss[grp];
+    for (int q = t; q < ng * ng; q += NT) S[q] = 0.f;
+    group_sync<NT>();
+    int* X = Xs[grp];
+    for (int p = 0; p < k; ++p) {
+      const int gn = v.pu_gn[e0 + p], gb = v.pu_gb[e0 + p];
+      if (gn == 0) continue;
+      const float* G = v.ginv_pool + v.u_goff[u] + v.pu_ginv[e0 + p];
+      for (int c = t; c < gn; c += NT) X[c] = v.o_x[v.sh_slot[O + gb + c]] - O;
+      group_sync<NT>();
+      // thread t adds the entries (a, c) with c = t % gn .. of its column
+      for (int q = t; q < gn * gn; q += NT) {
+        const int a = q / gn, c = q - a * gn;
+        S[X[a] * ng + X[c]] += G[q];
+      }
+      group_sync<NT>();
+    }
+    for (int x = t; x < ng; x += NT) S[x * ng + x] -= lam * (float)(v.g_cnt[O + x] - 1);
+    group_sync<NT>();
+    float m[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int i = rb * RB + r;
+      m[r] = (i < ng && j < ng) ? S[i * ng + j] : (i == j ? 1.f : 0.f);
+    }
+    if (!strip_gj<NP, RB, NT>(m, t, Cs[grp], Rs[grp])) {
+      if (t == 0) give_up_unit(v, u, 5);
+      continue;
+    }
+    float* dst = v.sinv_pool + v.u_soff[u];
+    if (j < ng) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int i = rb * RB + r;
+        if (i < ng) dst[i * ng + j] = m[r];
+      }
+    }
+  }
+}
+
 // the same for units with more than kUWarpGamma shared nodes: one CTA per unit,
 // S in dynamic shared memory, Gauss-Jordan sweeps by the whole CTA (warps take
 // rows, lanes columns)
 __global__ void __launch_bounds__(256) k_u_sinv_big(StepView v) {
   extern __shared__ __align__(16) float Sb[];
+  __shared__ int Xb[kUMaxGp];         // a piece's shared members as indices into S
   if (aborted_cta(v)) return;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int32_t nu = v.wfast[kWUnits];
@@ -406,9 +601,11 @@ __global__ void __launch_bounds__(256) k_u_sinv_big(StepView v) {
     for (int p = 0; p < k; ++p) {           // pieces in order: a fixed summation order
       const int gn = v.pu_gn[e0 + p], gb = v.pu_gb[e0 + p];
       const float* G = v.ginv_pool + v.u_goff[u] + v.pu_ginv[e0 + p];
+      for (int c = tid; c < gn; c += nt) Xb[c] = v.o_x[v.sh_slot[O + gb + c]] - O;
+      __syncthreads();
       for (int a = wid; a < gn; a += nw) {
-        const int xa = v.o_x[v.sh_slot[O + gb + a]] - O;
-        for (int c = lane; c < gn; c += 32) Sb[xa * ng + (v.o_x[v.sh_slot[O + gb + c]] - O)] += G[a * gn + c];
+        const int xa = Xb[a];
+        for (int c = lane; c < gn; c += 32) Sb[xa * ng + Xb[c]] += G[a * gn + c];
       }
       __syncthreads();
     }
@@ -532,7 +729,7 @@ __global__ void __launch_bounds__(kUWarps * 32) k_u_schur(StepView v) {
       const float* G = v.ginv_pool + v.u_goff[u] + v.pu_ginv[e0 + p];
       for (int a = lane; a < gn; a += 32) {
         float acc = 0.f;
-        for (int c = 0; c < gn; ++c) acc = fmaf(G[a * gn + c], th[gb + c], acc);
+        for (int c = 0; c < gn; ++c) acc = fmaf(G[c * gn + a], th[gb + c], acc);   // symmetric: column reads
         v.sh_tt[O + gb + a] = acc;
       }
     }
@@ -560,7 +757,7 @@ __global__ void __launch_bounds__(kUWarps * 32) k_u_schur(StepView v) {
       const float* G = v.ginv_pool + v.u_goff[u] + v.pu_ginv[e0 + p];
       for (int a = lane; a < gn; a += 32) {
         float acc = 0.f;
-        for (int c = 0; c < gn; ++c) acc = fmaf(G[a * gn + c], th[gb + c], acc);
+        for (int c = 0; c < gn; ++c) acc = fmaf(G[c * gn + a], th[gb + c], acc);   // symmetric: column reads
         v.sh_tt[O + gb + a] = acc;
       }
     }
@@ -707,7 +904,7 @@ cudaError_t configure_units_kernels() {
                               (int)(kUMaxGamma * kUMaxGamma * sizeof(float)));
 }
 
-cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st) {
+cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st, cudaEvent_t mid) {
   const int gw = num_sms * 4;            // CTAs of the per-unit kernels (kUWarps warps each)
   const int gt = num_sms * 8;            // CTAs of the per-occurrence kernels
   int32_t* n_units = v.wfast + kWUnits;
@@ -716,12 +913,18 @@ cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t
   k_u_occ<<<gw * (kUWarps / kUOccWarps), kUOccWarps * 32, 0, st>>>(v);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_gsz, n_units, v.u_goff, v.ginv_cap, v.wfast);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_ssz, n_units, v.u_soff, v.sinv_cap, v.wfast);
-  k_u_ginv<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
-  k_u_ginv<32, 64, 2><<<num_sms * 7, 64, 0, st>>>(v);
-  k_u_ginv<64, 96, 1><<<num_sms * 2, 32, 0, st>>>(v);
-  k_u_sinv<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
-  k_u_sinv<32, 64, 2><<<num_sms * 7, 64, 0, st>>>(v);
+  // (A_p[G,G])^-1 and S^-1 by size class: a warp per matrix in shared memory up
+  // to 32 nodes, a CTA per matrix in registers above (strips of 16 and 24 rows)
+  k_u_ginv_w<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
+  k_u_ginv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, st>>>(v);
+  k_u_ginv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, st>>>(v);
+  k_u_sinv_w<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
+  k_u_sinv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, st>>>(v);
   k_u_sinv_big<<<num_sms, 256, kUMaxGamma * kUMaxGamma * sizeof(float), st>>>(v);
+  if (mid) {
+    const cudaError_t e = cudaEventRecord(mid, st);
+    if (e != cudaSuccess) return e;
+  }
   k_u_init<<<gt, kUTh, 0, st>>>(v);
   for (int r = 0; r < 2; ++r) {
     if (r > 0) {

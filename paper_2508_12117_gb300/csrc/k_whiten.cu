@@ -920,7 +920,7 @@ int piece_cc_grid(int num_sms) {
 // solved on the side stream while the units are solved on st
 cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[4],
                                int clean_grid, cudaStream_t st, cudaStream_t side, cudaEvent_t fork,
-                               cudaEvent_t join) {
+                               cudaEvent_t join, const cudaEvent_t* ev, int clean_share) {
   if (!v.whiten) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(v.wfast, 0, kWSlots * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
@@ -937,17 +937,29 @@ cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc
   k_unit_ids<<<(unsigned)n_b, 256, 0, st>>>(v);
   k_unit_scan<<<1, 1024, 0, st>>>(v);
   k_unit_fill<<<(unsigned)n_b, 256, 0, st>>>(v);
-  if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
-  if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
-  k_whiten_clean<<<clean_grid, kCleanWarps * 32, 0, side>>>(v, tol);
-  if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+  // the clean pieces: on the side stream with clean_share / 4 of the
+  // persistent grid, concurrently with the units; clean_share 0: on st after them
+  if (clean_share > 0) {
+    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+    const int g = clean_grid * clean_share / 4;
+    k_whiten_clean<<<g > 0 ? g : 1, kCleanWarps * 32, 0, side>>>(v, tol);
+    if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+  }
   // units: data-parallel, then the CTA passes for the units it handed over
-  e = launch_units(v, tol, grids[3], st);
+  e = launch_units(v, tol, grids[3], st, ev ? ev[1] : nullptr);
   if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   k_whiten_units<KW1><<<grids[1], 256, sizeof(Smem1), st>>>(v, tol);
   k_whiten_units<KW2><<<grids[2], 256, sizeof(Smem2), st>>>(v, tol);
-  if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
+  if (clean_share == 0)
+    k_whiten_clean<<<clean_grid, kCleanWarps * 32, 0, st>>>(v, tol);
+  else if ((e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess)
+    return e;
   k_whiten_stats<<<1, 32, 0, st>>>(v);
+  if (ev && (e = cudaEventRecord(ev[4], st)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

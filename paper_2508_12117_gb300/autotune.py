@@ -61,6 +61,7 @@ def autotune(ctx: Context, eps: float, precision: int, hidden: int, steps: int =
     best = None
     for knobs in candidates(precision):
         ctx.spider_set_tuning(knobs)
+        ctx.spider_set_state(theta, step)          # every candidate steps from the same state
         ctx.spider_sgld_step(eps, seed0)          # captures the step graph for this shape
         ctx.spider_sync()
         t = time.perf_counter()

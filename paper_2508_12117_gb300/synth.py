@@ -120,14 +120,21 @@ def batch_specs(n: int = 16, minibatch: int = 1 << 18) -> List[Spec]:
     noise), all read through one 6 -> 4 x 128 network; minibatches of
     `minibatch` observations per catalog."""
     rng = np.random.default_rng(SEED_BASE + 5)
-    out = []
+    draws = []
     for c in range(n):
         M = int(round(math.exp(rng.uniform(math.log(1000.0), math.log(200000.0)))))
         S = int(rng.integers(20, 151))
         K = int(rng.integers(10, 26))
+        draws.append((M, S, K))
+    # one step size for every sub-problem (a batched step takes one eps): inside
+    # the stability bound of the catalog with the most observations per
+    # minibatch observation (about M K 10 dd observations per catalog)
+    n_over_b = max(M * K * 10 for M, _, K in draws) / minibatch
+    out = []
+    for c, (M, S, K) in enumerate(draws):
         nf = max(1, int(round(M / 2000)))
         region = max(10.0, 150.0 * math.sqrt(nf / 500.0))
-        h = Hyper(sigma=0.005, eps=_eps_for(0.03, 10, 20.0), batch_n=minibatch)
+        h = Hyper(sigma=0.005, eps=_eps_for(0.03, 20, n_over_b), batch_n=minibatch)
         out.append(Spec(f"batch{c:02d}-{M}ev", 50 + c, M, S, K, 10, "faults", n_faults=nf,
                         region_km=region, medium="gradient", noise="normal", noise_s=0.005,
                         forward="mlp", hidden=128, hyper=h))

@@ -10,6 +10,7 @@ larger than L2; each step reads a fresh random 2% of them.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8]
                   [--impl ours|reference] [--workload 4|3|2|1|5] [--no-forms]
+                  [--no-cpu-baseline] [--scale-events N]
 
 The headline form is BF16 (tensor-core hidden layers); the FP32 and FP8 forms of
 the same step are timed on the same catalog afterwards and reported under
@@ -111,17 +112,21 @@ def replica_rate(world, steps, ms):
 
 
 # ---------------------------------------------------------------- workload
-def build_workload(wid: int):
+def build_workload(wid: int, scale_events: int = 0):
+    """The workload's catalog, or (scale_events > 0) a smaller catalog drawn
+    with the same recipe (fault density, neighbours, stations per event) and
+    minibatches covering the same fraction of it."""
     from paper_2508_12117_gb300 import synth
     t = time.time()
-    cat = synth.make_catalog(wid)
+    if scale_events > 0:
+        s = synth.spec(wid)
+        bn = s.hyper.batch_n
+        if bn > 0:
+            bn = max(s.hyper.block_obs, int(bn * scale_events / s.n_events) // s.hyper.block_obs * s.hyper.block_obs)
+        cat = synth.make_catalog(synth.scaled_spec(wid, scale_events, batch_n=bn))
+    else:
+        cat = synth.make_catalog(wid)
     return cat, time.time() - t
-
-
-def launches_per_step(whiten: bool) -> int:
-    # selection + pair table 5, travel times 1, residuals 1, whitening (CSR
-    # assembly 4, components 15, work list 2, solvers 3 + merge 1), scatter/update 5
-    return 5 + 1 + 1 + (26 if whiten else 0) + 5
 
 
 # DRAM bytes (read + write) per unique pair of the BF16 tensor-core MLP kernel, from
@@ -224,7 +229,7 @@ def run_ours(args, rank, world):
     import torch
     from paper_2508_12117_gb300 import binding, synth
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    cat, t_gen = build_workload(args.workload)
+    cat, t_gen = build_workload(args.workload, args.scale_events)
     prec = {"fp32": binding.FP32, "bf16": binding.BF16, "fp8": binding.FP8}[args.precision]
     h = cat.spec.hyper
     stream = torch.cuda.Stream()
@@ -271,6 +276,7 @@ def run_ours(args, rank, world):
     ctx.spider_set_timing(False)
     ctx.spider_sgld_step(eps, seed0 + 9_999)        # capture + first launch, untimed
     torch.cuda.synchronize()
+    graph_kernels = ctx.spider_info()["graph_kernels"]      # kernel nodes of the step graph
     ev0.record(stream)
     for s in range(args.steps):
         ctx.spider_sgld_step(eps, seed0 + 10_000 + s)
@@ -321,7 +327,8 @@ def run_ours(args, rank, world):
     steps_s = replica_rate(world, K, ms_dev)
     state_bytes = cat.M * 32
     line = {
-        "metric": METRIC if args.workload == 4 else f"SGLD steps/s ({cat.spec.name})", "value": steps_s, "unit": "steps/s", "n_gpus": world, "steps": K,
+        "metric": METRIC if args.workload == 4 and not args.scale_events else f"SGLD steps/s ({cat.spec.name})",
+        "value": steps_s, "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_dev / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": cat.spec.name, "events": cat.M, "stations": cat.S, "dd_obs": cat.N,
@@ -347,7 +354,7 @@ def run_ours(args, rank, world):
                         "page-locked host buffer (M x 4 FP64) per step"},
         "forms": dict(forms, **({"bf16_over_fp32": steps_s / forms["fp32"]["value"]}
                                 if args.precision == "bf16" and "fp32" in forms else {})),
-        "gpu_launches": launches_per_step(cat.spec.hyper.kappa > 0) * K,
+        "gpu_launches": graph_kernels * K,
         "clocks": clk,
         "setup_s": {"generate": t_gen, "create": t_create},
     }
@@ -483,13 +490,15 @@ def run_batched(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic",
-            "config": {"workload": "16 catalogs (1k-200k events, log-uniform) x 4 chains",
+            "config": {"workload": f"{len(cats)} catalogs ({min(c.M for c in cats)}-{max(c.M for c in cats)} "
+                                   f"events, drawn log-uniform in 1k-200k) x {chains} chains",
                        "events": sum(c.M for c in cats) * chains, "dd_obs": sum(c.N for c in cats) * chains,
                        "minibatch_obs_per_catalog": h.batch_n, "mlp": "6-4x128-1",
                        "l2": "inputs larger than L2"},
             "sequential": {"value": n_sub * 1e3 / ms_seq, "ms_per_round": ms_seq,
                            "note": "each sampler in its own context, stepped one after another"},
             "speedup_vs_sequential": ms_seq / ms_batch, "graph": info["graph"], "tuning": list(knobs),
+            "gpu_launches": info["graph_kernels"] * args.steps,
             "tuning_ms": {k: v * 1e3 for k, v in tunings.items()}, "clocks": clk,
             "setup_s": {"generate": t_gen, "create": t_create}}
 
@@ -524,9 +533,9 @@ def oracle_step(cat, seed):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    cat, t_gen = build_workload(args.workload)
+    cat, t_gen = build_workload(args.workload, args.scale_events)
     base, secs = oracle_step(cat, 1_000_003 + 10_000)
-    metric = METRIC if args.workload == 4 else f"SGLD steps/s ({cat.spec.name})"
+    metric = METRIC if args.workload == 4 and not args.scale_events else f"SGLD steps/s ({cat.spec.name})"
     return {"impl": "reference", "metric": metric, "value": base["value"], "unit": "steps/s",
             "n_gpus": world, "steps": 1, "warmup": 0, "steps_requested": args.steps,
             "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -557,6 +566,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale-events", type=int, default=0,
+                    help="a smaller catalog of the workload's recipe with this many events "
+                         "(profiling captures; not a bench line)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

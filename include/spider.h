@@ -325,7 +325,8 @@ int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
  * the units solved; [31..37] units the data-parallel unit solver handed to
  * the CTA passes since the context was created, by reason: too many pieces,
  * shared occurrences, shared nodes, shared nodes of one piece, a failed small
- * inverse, a failed inverse of S, a full pool. */
+ * inverse, a failed inverse of S, a full pool; [38] kernel launches in the
+ * captured step graph (0 until a graph step ran). */
 int spider_info(spider_ctx *ctx, int64_t *out, int32_t n);
 
 /* Sampler diagnostics of Sec. 3.6 at the current state, accumulated in FP64 on

@@ -384,14 +384,15 @@ class Context:
         _check(load_library().spider_set_tuning(self.h, _ptr(arr, C.c_int32), arr.size), self.h)
 
     def spider_info(self):
-        out = np.zeros(38, np.int64)
-        _check(load_library().spider_info(self.h, _ptr(out, C.c_int64), 38), self.h)
+        out = np.zeros(39, np.int64)
+        _check(load_library().spider_info(self.h, _ptr(out, C.c_int64), 39), self.h)
         keys = ["n_sub", "graph", "blocks_per_step", "blocks", "pairs", "events", "obs", "components",
                 "local_nodes", "piece_inverses", "piece_whitening", "units", "fallback", "units_global",
                 "unit_kcycles_shared", "unit_kcycles_global"]
         keys += [f"pass{p}_{n}" for p in range(3) for n in ("setup", "ginv", "sinv", "rounds", "units")]
         keys += [f"handover_{n}" for n in ("pieces", "shared_occ", "shared_nodes", "piece_shared", "ginv_fail",
                                            "sinv_fail", "pool")]
+        keys += ["graph_kernels"]
         return dict(zip(keys, (int(x) for x in out)))
 
     def spider_diagnostics(self, batch_seed: int, eps: float):

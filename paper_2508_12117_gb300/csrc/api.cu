@@ -60,6 +60,7 @@ struct spider_ctx {
   cudaEvent_t ev[kEv] = {};
   cudaEvent_t wev[5] = {};          // whitening phases (timed evaluations of the piece path)
   bool have_wtiming = false;
+  int64_t graph_kernels = 0;        // kernel nodes of the captured step graph
   float last_ms[5] = {0, 0, 0, 0, 0};
   bool have_timing = false;
 };
@@ -301,6 +302,18 @@ int evaluate(spider_ctx* c, uint64_t seed, int mode, float eps) {
       if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
           cudaGraphInstantiate(&c->graph_exec, g, 0) == cudaSuccess) {
         c->graph = g;
+        // kernel launches per graph step (what the step runs on the device)
+        size_t nn = 0;
+        c->graph_kernels = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+          std::vector<cudaGraphNode_t> nodes(nn);
+          if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+            for (size_t i = 0; i < nn; ++i) {
+              cudaGraphNodeType ty;
+              if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                ++c->graph_kernels;
+            }
+        }
       } else {
         if (g) cudaGraphDestroy(g);
         c->graph_exec = nullptr;
@@ -1230,12 +1243,13 @@ int spider_info(spider_ctx* c, int64_t* out, int32_t n) {
     CK(c, cudaMemcpyAsync(wf, c->v.wfast, sizeof(wf), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
   }
-  int64_t vals[38] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
+  int64_t vals[39] = {c->n_sub, c->graph_exec ? 1 : 0, c->nb_mb, c->nb_full, c->v.P, c->v.M, c->v.N,
                       cnt[kCntComps], c->v.Q, c->fast ? 1 : 0, c->fast ? (c->mb_full_sub ? 0 : 1) : 0,
                       wf[kWUnits], wf[kWGeneral], wf[kWBigS], wf[kWCycSm], wf[kWCycBig]};
   for (int i = 0; i < 15; ++i) vals[16 + i] = wf[kWSlots + 64 + i];
   for (int i = 0; i < 7; ++i) vals[31 + i] = wf[kWSlots + 64 + 16 + i];
-  for (int32_t i = 0; i < n && i < 38; ++i) out[i] = vals[i];
+  vals[38] = c->graph_kernels;
+  for (int32_t i = 0; i < n && i < 39; ++i) out[i] = vals[i];
   return SPIDER_OK;
 }
 

@@ -31,7 +31,7 @@ namespace {
 constexpr int kUMaxPieces = 32;    // pieces of a unit
 constexpr int kUMaxShared = 1024;  // shared occurrences of a unit
 constexpr int kUMaxGamma = 192;    // shared nodes of a unit
-constexpr int kUWarpGamma = 64;    // S^-1 by one warp up to this size, by a CTA above
+constexpr int kUStripGamma = 96;   // S^-1 in registers up to this size, in shared memory above
 constexpr int kUMaxGp = 96;        // shared nodes of one piece
 constexpr int kUWarps = 8;         // warps per CTA of the per-unit kernels
 constexpr int kUOccWarps = 4;      // warps per CTA of k_u_occ (a sort buffer of kUMaxShared keys each)
@@ -576,9 +576,10 @@ __global__ void __launch_bounds__(NT * GROUPS) k_u_sinv(StepView v) {
   }
 }
 
-// the same for units with more than kUWarpGamma shared nodes: one CTA per unit,
-// S in dynamic shared memory, Gauss-Jordan sweeps by the whole CTA (warps take
-// rows, lanes columns)
+// the same for units with more than kUStripGamma shared nodes: one CTA per
+// unit (taken from a work cursor, so that no CTA solves two of the few large
+// units while others idle), S in dynamic shared memory, Gauss-Jordan sweeps by
+// the whole CTA (warps take rows, lanes columns)
 __global__ void __launch_bounds__(256) k_u_sinv_big(StepView v) {
   extern __shared__ __align__(16) float Sb[];
   __shared__ int Xb[kUMaxGp];         // a piece's shared members as indices into S
@@ -586,10 +587,15 @@ __global__ void __launch_bounds__(256) k_u_sinv_big(StepView v) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int32_t nu = v.wfast[kWUnits];
   const float lam = v.lam;
-  __shared__ int bad;
-  for (int32_t u = blockIdx.x; u < nu; u += gridDim.x) {
+  __shared__ int bad, cur;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) cur = atomicAdd(&v.wfast[kWCursorS], 1);
+    __syncthreads();
+    const int32_t u = cur;
+    if (u >= nu) break;
     const int ng = v.u_ng[u];
-    if (ng <= kUWarpGamma) continue;
+    if (ng <= kUStripGamma) continue;
     const int32_t O = v.uocc_off[u], e0 = v.unit_off[u];
     const int k = v.unit_off[u + 1] - e0;
     if ((int64_t)v.u_soff[u] + (int64_t)ng * ng > v.sinv_cap || (int64_t)v.u_goff[nu] > v.ginv_cap) {
@@ -920,6 +926,7 @@ cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t
   k_u_ginv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, st>>>(v);
   k_u_sinv_w<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
   k_u_sinv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, st>>>(v);
+  k_u_sinv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, st>>>(v);
   k_u_sinv_big<<<num_sms, 256, kUMaxGamma * kUMaxGamma * sizeof(float), st>>>(v);
   if (mid) {
     const cudaError_t e = cudaEventRecord(mid, st);

@@ -253,6 +253,7 @@ enum : int {
   kWCursor0 = 11,  // work cursor of the one-warp unit pass
   kWDefer2 = 12,   // units deferred from the CTA pass to the last pass
   kWCycW = 13,     // SM cycles / 1024 spent on units of the one-warp pass
+  kWCursorS = 14,  // work cursor of the CTA inverse of the largest S
   kWSlots = 16
 };
 constexpr int kCenChunk = 4096;   // events per centroid partial sum

@@ -31,7 +31,6 @@ namespace {
 constexpr int kUMaxPieces = 32;    // pieces of a unit
 constexpr int kUMaxShared = 1024;  // shared occurrences of a unit
 constexpr int kUMaxGamma = 192;    // shared nodes of a unit
-constexpr int kUStripGamma = 96;   // S^-1 in registers up to this size, in shared memory above
 constexpr int kUMaxGp = 96;        // shared nodes of one piece
 constexpr int kUWarps = 8;         // warps per CTA of the per-unit kernels
 constexpr int kUOccWarps = 4;      // warps per CTA of k_u_occ (a sort buffer of kUMaxShared keys each)
@@ -576,7 +575,72 @@ __global__ void __launch_bounds__(NT * GROUPS) k_u_sinv(StepView v) {
   }
 }
 
-// the same for units with more than kUStripGamma shared nodes: one CTA per
+// the same for units with MINN < ng <= NP whose S does not fit in static shared
+// memory: one CTA per unit from the work cursor wfast[CURSOR], S assembled in
+// dynamic shared memory (NP x NP floats), S^-1 by strip_gj in registers
+template <int MINN, int NP, int RB, int NT, int CURSOR>
+__global__ void __launch_bounds__(NT) k_u_sinv_d(StepView v) {
+  extern __shared__ __align__(16) float Sd[];
+  __shared__ float Cs[2 * NP], Rs[2 * NP];
+  __shared__ int Xs[kUMaxGp];
+  __shared__ int cur;
+  if (aborted_cta(v)) return;
+  const int t = threadIdx.x;
+  const int j = t % NP, rb = t / NP;
+  const int32_t nu = v.wfast[kWUnits];
+  const float lam = v.lam;
+  for (;;) {
+    __syncthreads();
+    if (t == 0) cur = atomicAdd(&v.wfast[CURSOR], 1);
+    __syncthreads();
+    const int32_t u = cur;
+    if (u >= nu) break;
+    const int ng = v.u_ng[u];
+    if (ng <= MINN || ng > NP) continue;
+    const int32_t O = v.uocc_off[u], e0 = v.unit_off[u];
+    const int k = v.unit_off[u + 1] - e0;
+    if ((int64_t)v.u_soff[u] + (int64_t)ng * ng > v.sinv_cap || (int64_t)v.u_goff[nu] > v.ginv_cap) {
+      if (t == 0) give_up_unit(v, u, 6);
+      continue;
+    }
+    for (int q = t; q < ng * ng; q += NT) Sd[q] = 0.f;
+    __syncthreads();
+    for (int p = 0; p < k; ++p) {           // pieces in order: a fixed summation order
+      const int gn = v.pu_gn[e0 + p], gb = v.pu_gb[e0 + p];
+      if (gn == 0) continue;
+      const float* G = v.ginv_pool + v.u_goff[u] + v.pu_ginv[e0 + p];
+      for (int c = t; c < gn; c += NT) Xs[c] = v.o_x[v.sh_slot[O + gb + c]] - O;
+      __syncthreads();
+      for (int q = t; q < gn * gn; q += NT) {
+        const int a = q / gn, c = q - a * gn;
+        Sd[Xs[a] * ng + Xs[c]] += G[q];
+      }
+      __syncthreads();
+    }
+    for (int x = t; x < ng; x += NT) Sd[x * ng + x] -= lam * (float)(v.g_cnt[O + x] - 1);
+    __syncthreads();
+    float m[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int i = rb * RB + r;
+      m[r] = (i < ng && j < ng) ? Sd[i * ng + j] : (i == j ? 1.f : 0.f);
+    }
+    if (!strip_gj<NP, RB, NT>(m, t, Cs, Rs)) {
+      if (t == 0) give_up_unit(v, u, 5);
+      continue;
+    }
+    float* dst = v.sinv_pool + v.u_soff[u];
+    if (j < ng) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int i = rb * RB + r;
+        if (i < ng) dst[i * ng + j] = m[r];
+      }
+    }
+  }
+}
+
+// the same for units with more than 128 shared nodes: one CTA per
 // unit (taken from a work cursor, so that no CTA solves two of the few large
 // units while others idle), S in dynamic shared memory, Gauss-Jordan sweeps by
 // the whole CTA (warps take rows, lanes columns)
@@ -595,7 +659,7 @@ __global__ void __launch_bounds__(256) k_u_sinv_big(StepView v) {
     const int32_t u = cur;
     if (u >= nu) break;
     const int ng = v.u_ng[u];
-    if (ng <= kUStripGamma) continue;
+    if (ng <= 128) continue;
     const int32_t O = v.uocc_off[u], e0 = v.unit_off[u];
     const int k = v.unit_off[u + 1] - e0;
     if ((int64_t)v.u_soff[u] + (int64_t)ng * ng > v.sinv_cap || (int64_t)v.u_goff[nu] > v.ginv_cap) {
@@ -906,8 +970,11 @@ __global__ void __launch_bounds__(kUWarps * 32) k_u_out(StepView v, float tol) {
 int units_grid(int num_sms) { return num_sms * 4; }
 
 cudaError_t configure_units_kernels() {
-  return cudaFuncSetAttribute(k_u_sinv_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kUMaxGamma * kUMaxGamma * sizeof(float)));
+  cudaError_t e = cudaFuncSetAttribute(k_u_sinv_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kUMaxGamma * kUMaxGamma * sizeof(float)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_u_sinv_d<96, 128, 32, 512, kWCursorS2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(128 * 128 * sizeof(float)));
 }
 
 cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st, cudaEvent_t mid) {
@@ -927,6 +994,7 @@ cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t
   k_u_sinv_w<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
   k_u_sinv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, st>>>(v);
   k_u_sinv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, st>>>(v);
+  k_u_sinv_d<96, 128, 32, 512, kWCursorS2><<<num_sms, 512, 128 * 128 * sizeof(float), st>>>(v);
   k_u_sinv_big<<<num_sms, 256, kUMaxGamma * kUMaxGamma * sizeof(float), st>>>(v);
   if (mid) {
     const cudaError_t e = cudaEventRecord(mid, st);

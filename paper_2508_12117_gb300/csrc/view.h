@@ -254,6 +254,7 @@ enum : int {
   kWDefer2 = 12,   // units deferred from the CTA pass to the last pass
   kWCycW = 13,     // SM cycles / 1024 spent on units of the one-warp pass
   kWCursorS = 14,  // work cursor of the CTA inverse of the largest S
+  kWCursorS2 = 15, // work cursor of the register inverse of S at 97..128 shared nodes
   kWSlots = 16
 };
 constexpr int kCenChunk = 4096;   // events per centroid partial sum

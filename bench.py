@@ -143,8 +143,7 @@ def flops_per_pair(H: int) -> float:
 
 def hbm_bytes(n_obs, q_nodes, p_u, M, touched, pairs_per_event, sampled):
     """Algorithmic DRAM bytes per launch of the HBM-bound step kernels (every
-    array element the kernel must read or write once; see the kernel table of
-    the design notes):
+    array element the kernel must read or write once):
       k_resid   20 B per observation (packed local indices, reduced dt, sqrt w,
                 the residual written, two half-edge codes) + 47 B per local node
                 (unique index, T hi/lo, pair, event, origin time, half-edge

@@ -7,8 +7,7 @@ reference legs may import or run anything in this directory; the product path
 It is a plain, slow, single-threaded restatement of what one SGLD step of
 SPIDER (Ross et al., arXiv 2508.12117) computes, in float64, written from the
 paper's definitions.  Each function names the passage it follows.  Where the
-paper is silent or ambiguous the reading taken is stated in the docstring
-(the same readings are listed in the design notes of the repository):
+paper is silent or ambiguous the reading taken is stated in the docstring:
 
   R1  centroid prior (Sec. 3.1, centroid equations): the prior is placed on
       the current catalog centroid mean_m(theta_m), centred on the centroid

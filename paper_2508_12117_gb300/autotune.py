@@ -2,7 +2,7 @@
 
 Times every candidate setting of the knobs of `spider_set_tuning` (warp- and
 CTA-solver grid multipliers, FP32 MLP CTAs per SM, the clean-piece solver's
-share of the grid beside the units) on a live context for a few SGLD steps,
+share of the grid beside the units, the residual kernels' CTA size) on a live context for a few SGLD steps,
 keeps the fastest, and caches it per workload signature in a JSON
 file (SPIDER_TUNE_CACHE, default ~/.cache/spider_gb300/tuning.json).  The knobs
 change speed only: results are identical for every setting.  The chain state is
@@ -22,9 +22,12 @@ CACHE = os.environ.get("SPIDER_TUNE_CACHE",
 
 def candidates(precision: int):
     """(warp-solver CTAs per SM slot, CTA-solver CTAs per SM, FP32 MLP CTAs per
-    SM, piece-inverse path on, clean-piece solver's quarters of the grid)."""
+    SM, piece-inverse path on, clean-piece solver's quarters of the grid, threads
+    per CTA of the per-block residual kernels in units of 256 -- the observations
+    per warp)."""
     mlp = (1, 2) if precision == FP32 else (2,)
-    return [(w, c, f, 1, q) for w in (1, 2, 4) for c in (1, 2) for f in mlp for q in (1, 2, 4)]
+    return [(w, c, f, 1, q, t) for w in (1, 2, 4) for c in (1, 2) for f in mlp for q in (1, 2, 4)
+            for t in (1, 2, 4)]
 
 
 def signature(ctx: Context, precision: int, hidden: int) -> str:

@@ -37,7 +37,7 @@ struct spider_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_ok = true;
   bool use_graph = true;
-  int32_t knobs[5] = {2, 1, 2, 1, 2};   // see spider_set_tuning
+  int32_t knobs[6] = {2, 1, 2, 1, 2, 2};   // see spider_set_tuning
   // whitening through precomputed piece inverses (minibatch steps)
   bool fast = false;               // tables built
   bool mb_full_sub = false;        // a sub-problem selects all its blocks in a minibatch
@@ -249,7 +249,7 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed, 
   TTOut out{v.T2, v.J};
   TRY(launch_tt(c->net, src, out, c->num_sms, c->tt_scratch, st, c->knobs[2]));
   if (timed) TRY(cudaEventRecord(c->ev[2], st));
-  TRY(launch_resid(v, n_b, c->gu, st, timed ? &c->ev[3] : nullptr));
+  TRY(launch_resid(v, n_b, c->gu, st, timed ? &c->ev[3] : nullptr, 256 * c->knobs[5]));
   if (fast) {
     TRY(launch_whiten_fast(v, n_b, c->cfg.pcg_tol, c->cc_grid, c->unit_grids, c->clean_grid, st, c->side,
                            c->fork, c->join, timed ? c->wev : nullptr, c->knobs[4]));
@@ -260,7 +260,7 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed, 
     TRY(launch_pcg(v, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
   }
   if (timed) TRY(cudaEventRecord(c->ev[5], st));
-  TRY(launch_finish(v, n_b, c->gu, logpost, st, timed ? &c->ev[6] : nullptr));
+  TRY(launch_finish(v, n_b, c->gu, logpost, st, timed ? &c->ev[6] : nullptr, 256 * c->knobs[5]));
 #undef TRY
   return cudaSuccess;
 }
@@ -1218,14 +1218,20 @@ int spider_debug_obs(spider_ctx* c, int64_t* idx_out, float* r_out, float* q_out
 
 int spider_set_tuning(spider_ctx* c, const int32_t* knobs, int32_t n) {
   if (!c || (n > 0 && !knobs)) return SPIDER_E_INVAL;
-  const int32_t lo[5] = {1, 1, 1, 0, 0}, hi[5] = {8, 4, 2, 1, 4};
-  for (int32_t i = 0; i < n && i < 5; ++i)
+  const int32_t lo[6] = {1, 1, 1, 0, 0, 1}, hi[6] = {8, 4, 2, 1, 4, 4};
+  for (int32_t i = 0; i < n && i < 6; ++i)
     if (knobs[i] < lo[i] || knobs[i] > hi[i]) {
       c->err = "tuning knob out of range";
       return SPIDER_E_INVAL;
     }
   CK(c, cudaStreamSynchronize(c->stream));
-  for (int32_t i = 0; i < n && i < 5; ++i) c->knobs[i] = knobs[i];
+  for (int32_t i = 0; i < n && i < 6; ++i) {
+    if (i == 5 && knobs[i] == 3) {
+      c->err = "tuning knob out of range";
+      return SPIDER_E_INVAL;
+    }
+    c->knobs[i] = knobs[i];
+  }
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;

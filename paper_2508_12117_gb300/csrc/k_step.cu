@@ -1829,8 +1829,9 @@ int pcg_grid(const StepView& v, int num_sms) {
 }
 
 // ev (or null): events recorded after k_resid and after k_merge_rhs
-cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st, const cudaEvent_t* ev) {
-  k_resid<<<(unsigned)n_b, kThreads, resid_smem(v), st>>>(v);
+cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st, const cudaEvent_t* ev,
+                         int bthreads) {
+  k_resid<<<(unsigned)n_b, bthreads, resid_smem(v), st>>>(v);
   if (ev) CK_LAUNCH(cudaEventRecord(ev[0], st));
   if (v.whiten) k_merge_rhs<<<gu, kThreads, 0, st>>>(v);
   if (ev) CK_LAUNCH(cudaEventRecord(ev[1], st));
@@ -1902,8 +1903,8 @@ cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, in
 
 // ev (or null): events recorded after k_final, k_merge_s, the centroid, k_event
 cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, cudaStream_t st,
-                          const cudaEvent_t* ev) {
-  k_final<<<(unsigned)n_b, kThreads, final_smem(v), st>>>(v);
+                          const cudaEvent_t* ev, int bthreads) {
+  k_final<<<(unsigned)n_b, bthreads, final_smem(v), st>>>(v);
   if (ev) CK_LAUNCH(cudaEventRecord(ev[0], st));
   k_merge_s<<<gu, kThreads, 0, st>>>(v);
   if (ev) CK_LAUNCH(cudaEventRecord(ev[1], st));

@@ -27,11 +27,15 @@ cudaError_t mlp_tc_prepare(const float* W1_host, const float* const Wn_host[3], 
 cudaError_t configure_step_kernels(const StepView& v);
 int pcg_grid(const StepView& v, int num_sms);
 cudaError_t launch_select(const StepView& v, int64_t n_b, cudaStream_t st);
-cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st, const cudaEvent_t* ev);
+// bthreads: threads per CTA of the per-block kernels k_resid and k_final (a
+// multiple of 32 up to 1024; results do not depend on it except the rounding
+// order of the FP64 r.q sums)
+cudaError_t launch_resid(const StepView& v, int64_t n_b, int gu, cudaStream_t st, const cudaEvent_t* ev,
+                         int bthreads = 256);
 cudaError_t launch_pcg(const StepView& v, int64_t n_b, int max_it, float tol, int grid, int warp_mult,
                        int cta_mult, cudaStream_t st);
 cudaError_t launch_finish(const StepView& v, int64_t n_b, int gu, bool logpost, cudaStream_t st,
-                          const cudaEvent_t* ev);
+                          const cudaEvent_t* ev, int bthreads = 256);
 // theta_0 + state (or a stored sample) in FP64, caller order (M x 4)
 cudaError_t launch_state_out(const StepView& v, const float4* src, double* out, int grid, cudaStream_t st);
 // the last gradient (FP32), caller order (M x 4)

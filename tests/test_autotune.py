@@ -10,7 +10,7 @@ from paper_2508_12117_gb300.binding import BF16, FP32
 
 class FakeContext:
     """Duck-types the calls the autotuner makes; a step sleeps for a time that
-    depends on the current knobs, with (2, 1, f, 1, 2) the fastest."""
+    depends on the current knobs, with (2, 1, f, 1, 2, 2) the fastest."""
 
     def __init__(self):
         self.knobs = None
@@ -27,8 +27,8 @@ class FakeContext:
         self.applied.append(self.knobs)
 
     def spider_sgld_step(self, eps, seed):
-        w, c, f, _, q = self.knobs
-        time.sleep(0.002 * (abs(w - 2) + abs(c - 1) + abs(q - 2)) + 0.0005)
+        w, c, f, _, q, t = self.knobs
+        time.sleep(0.002 * (abs(w - 2) + abs(c - 1) + abs(q - 2) + abs(t - 2)) + 0.0005)
         self.steps += 1
 
     def spider_sync(self):
@@ -42,8 +42,8 @@ class FakeContext:
 
 
 def test_candidates_cover_the_knobs():
-    assert len(autotune.candidates(FP32)) == 36          # 3 warp x 2 CTA x 2 FP32-MLP x 3 clean shares
-    assert len(autotune.candidates(BF16)) == 18
+    assert len(autotune.candidates(FP32)) == 108         # 3 warp x 2 CTA x 2 FP32-MLP x 3 clean x 3 CTA sizes
+    assert len(autotune.candidates(BF16)) == 54
     assert all(k[2] == 2 and k[3] == 1 for k in autotune.candidates(BF16))
 
 
@@ -51,16 +51,16 @@ def test_autotune_picks_fastest_restores_state_and_caches(tmp_path):
     path = str(tmp_path / "tune.json")
     ctx = FakeContext()
     knobs, timings = autotune.autotune(ctx, 1e-4, BF16, 128, steps=2, path=path, use_cache=True)
-    assert knobs == (2, 1, 2, 1, 2)
-    assert ctx.knobs == (2, 1, 2, 1, 2)                   # the choice is left applied
+    assert knobs == (2, 1, 2, 1, 2, 2)
+    assert ctx.knobs == (2, 1, 2, 1, 2, 2)                # the choice is left applied
     assert ctx.restored == ctx.state                      # tuning does not advance the sampler
     assert len(timings) == len(autotune.candidates(BF16))
     assert ctx.steps == 3 * len(timings)                  # one capture step + 2 timed per candidate
 
     again = FakeContext()
     k2, t2 = autotune.autotune(again, 1e-4, BF16, 128, path=path, use_cache=True)
-    assert k2 == (2, 1, 2, 1, 2) and t2 == {} and again.steps == 0
-    assert again.applied == [(2, 1, 2, 1, 2)]
+    assert k2 == (2, 1, 2, 1, 2, 2) and t2 == {} and again.steps == 0
+    assert again.applied == [(2, 1, 2, 1, 2, 2)]
 
 
 def test_signature_separates_workloads():

@@ -130,10 +130,10 @@ def build_workload(wid: int, scale_events: int = 0):
 
 
 # DRAM bytes (read + write) per unique pair of the BF16 tensor-core MLP kernel, from
-# one ncu capture of the 100k-event step (8.42 MB read, 0.06 MB written, for about
-# 0.372 M pairs; profiles/k_tt_mlp_tc_bf16_100kev.md); scaled by the pairs of a
-# launch.  Only valid while that kernel is unchanged.
-MLP_BF16_DRAM_BYTES_PER_PAIR = (8.423168e6 + 0.060160e6) / 372371.5
+# one ncu capture of a 100k-event catalog of the 1M-event recipe (4.42 MB read,
+# 0.8 KB written, for about 0.160 M pairs; profiles/k_tt_mlp_tc_bf16_100kev.md);
+# scaled by the pairs of a launch.  Only valid while that kernel is unchanged.
+MLP_BF16_DRAM_BYTES_PER_PAIR = (4.421632e6 + 768.0) / 160303.5
 
 
 def flops_per_pair(H: int) -> float:

@@ -307,9 +307,10 @@ int spider_debug_obs(spider_ctx *ctx, int64_t *idx_out, float *r_out, float *q_o
  * (0..4, default 2) the share, in quarters, of the persistent grid the
  * clean-piece solver takes on its side stream while the units are solved
  * (0: it runs after them on the context's stream); knobs[5] (1, 2 (default)
- * or 4) threads per CTA of the per-block residual and whitened-residual kernels, in
- * units of 256 (the observations each thread handles; changes only the
- * rounding order of the FP64 log-likelihood sum).  Invalidates the captured step graph. */
+ * or 4) threads per CTA of the per-block kernels (pair table, residuals,
+ * whitened residuals), in units of 256 (the observations and nodes each thread
+ * handles; changes only the rounding order of the FP64 log-likelihood sum).
+ * Invalidates the captured step graph. */
 int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
 
 /* Facts about a context (synchronous), out[0..n): [0] sub-problems,

@@ -233,7 +233,7 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed, 
   TRY(cudaMemsetAsync(v.counters, 0, 3 * sizeof(int32_t), st));
   TRY(cudaMemsetAsync(v.counters + kCntBarArrive, 0, (kCntSlots - kCntBarArrive) * sizeof(int32_t), st));
   TRY(cudaMemsetAsync(v.sub_nsel, 0, c->n_sub * sizeof(int32_t), st));
-  TRY(launch_select(v, n_b, st));
+  TRY(launch_select(v, n_b, st, 256 * c->knobs[5]));
   if (timed) TRY(cudaEventRecord(c->ev[1], st));
   PairSource src{};
   src.uniq_pair = v.uniq_pair;

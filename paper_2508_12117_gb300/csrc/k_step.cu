@@ -1788,12 +1788,12 @@ __global__ void k_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t
 
 static inline int grid_for(int64_t n, int t = kThreads) { return (int)((n + t - 1) / t); }
 
-cudaError_t launch_select(const StepView& v, int64_t n_b, cudaStream_t st) {
+cudaError_t launch_select(const StepView& v, int64_t n_b, cudaStream_t st, int bthreads) {
   k_select<<<grid_for(n_b), kThreads, 0, st>>>(v, n_b);
-  k_owner<<<(unsigned)n_b, kThreads, 0, st>>>(v);
+  k_owner<<<(unsigned)n_b, bthreads, 0, st>>>(v);
   k_scan_owner<<<1, 1024, 0, st>>>(v, n_b);
-  k_assign<<<(unsigned)n_b, kThreads, 0, st>>>(v);
-  k_link<<<(unsigned)n_b, kThreads, 0, st>>>(v);
+  k_assign<<<(unsigned)n_b, bthreads, 0, st>>>(v);
+  k_link<<<(unsigned)n_b, bthreads, 0, st>>>(v);
   return cudaGetLastError();
 }
 

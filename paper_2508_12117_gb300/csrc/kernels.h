@@ -26,7 +26,7 @@ cudaError_t mlp_tc_prepare(const float* W1_host, const float* const Wn_host[3], 
 // step (k_step.cu)
 cudaError_t configure_step_kernels(const StepView& v);
 int pcg_grid(const StepView& v, int num_sms);
-cudaError_t launch_select(const StepView& v, int64_t n_b, cudaStream_t st);
+cudaError_t launch_select(const StepView& v, int64_t n_b, cudaStream_t st, int bthreads = 256);
 // bthreads: threads per CTA of the per-block kernels k_resid and k_final (a
 // multiple of 32 up to 1024; results do not depend on it except the rounding
 // order of the FP64 r.q sums)

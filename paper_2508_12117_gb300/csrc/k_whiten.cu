@@ -15,9 +15,11 @@
 //        z_I = A_p[I,I] f_I + A_p[I,G] (A_p[G,G])^-1 (z_G - A_p[G,I] f_I)
 //     (c = the number of pieces holding a shared node; each piece's matrix
 //     carries lambda once, the unit's matrix once per node), refined like the
-//     single pieces (one CTA per unit).
-// A unit beyond the shared-memory limits, or one that does not converge, sets
-// a flag on which the general component solver then runs for the whole step.
+//     single pieces: by the data-parallel unit solver (k_units.cu), and the
+//     units beyond its limits here, one CTA per unit in two passes by size
+//     (k_whiten_units, MODE 1 and 2).
+// A unit beyond every limit, or one that does not converge, sets a flag on
+// which the general component solver then runs for the whole step.
 // Every sum runs in a fixed order, so the result is reproducible.
 #include <cuda_runtime.h>
 
@@ -863,20 +865,15 @@ __global__ void k_whiten_stats(StepView v) {
 
 }  // namespace
 
-// the three passes: <pieces, members, shared nodes, S^-1 and small inverses in
-// shared memory, threads>
-#define KW0 8, 256, 32, 32, 1536, 32, 0
+// the two CTA passes for the units the data-parallel solver hands over:
+// <pieces, members, shared nodes, S^-1 and small inverses in shared memory, threads>
 #define KW1 32, 1024, 256, 64, 4096, 256, 1
 #define KW2 32, 1024, 256, 160, 8192, 256, 2
-using Smem0 = UnitSmem<8, 256, 32, 32, 1536>;
 using Smem1 = UnitSmem<32, 1024, 256, 64, 4096>;
 using Smem2 = UnitSmem<32, 1024, 256, 160, 8192>;
 
 cudaError_t configure_whiten_kernels() {
   cudaError_t e = configure_units_kernels();
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_whiten_units<KW0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(Smem0));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_whiten_units<KW1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem1));
   if (e != cudaSuccess) return e;
@@ -888,18 +885,18 @@ int piece_max_nodes() { return kPieceMaxDev; }
 
 int64_t whiten_unit_scratch_floats() { return kUScratch; }
 
-// CTAs of the three unit passes (0 when one of them cannot run on this device)
+// CTAs of the two CTA unit passes in grids[1], grids[2] (returns 0 when one of
+// them cannot run on this device)
 int whiten_units_grids(int num_sms, int grids[3]) {
-  int a = 0, b = 0, c = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_whiten_units<KW0>, 32, sizeof(Smem0)) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_whiten_units<KW1>, 256, sizeof(Smem1)) != cudaSuccess ||
+  int b = 0, c = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_whiten_units<KW1>, 256, sizeof(Smem1)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_whiten_units<KW2>, 256, sizeof(Smem2)) != cudaSuccess ||
-      a < 1 || b < 1 || c < 1)
+      b < 1 || c < 1)
     return 0;
-  grids[0] = num_sms * a;
+  grids[0] = 0;
   grids[1] = num_sms * b;
   grids[2] = num_sms * c;
-  return grids[0];
+  return grids[1];
 }
 
 int whiten_clean_grid(int num_sms) {

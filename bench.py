@@ -335,7 +335,7 @@ def run_ours(args, rank, world):
                    "mlp": f"6-4x{H}-1" if H else "analytic homogeneous",
                    "precision": args.precision,
                    "l2": ("inputs larger than L2 (tables of the catalog, fresh random blocks every step)"
-                          if cat.N > 20_000_000 else "inputs smaller than L2 (small workload)"),
+                          if cat.N * 12 > 129e6 else "inputs smaller than L2 (small workload)"),
                    "parallelism": f"replicas x{world}"},
         "dd_obs_per_s": world * n_per_step * K / (ms_dev * 1e-3),
         "pairs_per_step": p_per_step, "touched_events_per_step": touched / K,

@@ -66,3 +66,35 @@ def test_wait_limit_is_validated(cat1):
     with pytest.raises(binding.SpiderError):
         a.spider_set_wait_limit_ns(601 * 10 ** 9)
     a.close()
+
+
+def test_zero_wait_limit_in_a_piece_path_step():
+    """The same on a minibatch step whitened through the piece inverses: the
+    cooperative piece labelling (k_piece_cc) gives up at its first grid barrier,
+    the unit, clean-piece and scatter kernels see the error and return, the
+    state stays where it was, and after the limit is restored the chain is the
+    one a fresh context walks."""
+    cat = synth.make_catalog(2)
+    bn = 1 << 14
+    eps = synth._eps_for(0.03, 10, cat.N / bn)
+    a = binding.Context.from_catalog(cat, batch_n=bn)
+    ref = binding.Context.from_catalog(cat, batch_n=bn)
+    assert a.spider_info()["piece_whitening"] == 1
+    th0, _ = a.spider_get_state()
+    a.spider_set_wait_limit_ns(0)
+    a.spider_sgld_step(eps, 5)
+    with pytest.raises(binding.SpiderError) as e:
+        a.spider_sync()
+    assert e.value.code == SPIDER_E_TIMEOUT
+    th1, _ = a.spider_get_state()
+    assert np.array_equal(th1, th0)
+    a.spider_set_wait_limit_ns(2_000_000_000)
+    a.spider_set_state(th0, 0)
+    for s in (21, 22, 23):
+        a.spider_sgld_step(eps, s)
+        ref.spider_sgld_step(eps, s)
+    ta, _ = a.spider_get_state()
+    tr, _ = ref.spider_get_state()
+    assert np.array_equal(ta, tr)
+    a.close()
+    ref.close()

@@ -665,3 +665,63 @@ def test_calibration_of_an_exact_posterior_is_uniform():
     assert abs(c.mean() - 0.5) < 0.01 and abs(c.var() - 1 / 12) < 0.005
     # independent draws: ESS close to n
     assert abs(np.median(ess) / n - 1.0) < 0.15
+
+
+# ---------------------------------------------------------------- small helpers
+def test_box_muller_polar_form():
+    """z0 = R cos(2 pi u2), z1 = R sin(2 pi u2) with R^2 = -2 ln u1: the radius
+    and the angle of each pair recovered from the words (a swapped sine and
+    cosine or a dropped factor fails)."""
+    rng = np.random.default_rng(7)
+    wa = rng.integers(0, 2 ** 32, 1000, dtype=np.uint64)
+    wb = rng.integers(0, 2 ** 32, 1000, dtype=np.uint64)
+    z0, z1 = O.box_muller(wa, wb)
+    u1, u2 = O.unit_from_word(wa), O.unit_from_word(wb)
+    assert np.allclose(z0 * z0 + z1 * z1, -2.0 * np.log(u1), rtol=1e-12, atol=1e-15)
+    ang = np.mod(np.arctan2(z1, z0), 2 * math.pi)
+    d = np.abs(ang - 2 * math.pi * u2)
+    assert np.all(np.minimum(d, 2 * math.pi - d) < 1e-9)
+    # the smallest first word gives the largest radius, sqrt(-2 ln 2^-24)
+    z0, z1 = O.box_muller(np.array([0], np.uint64), np.array([0], np.uint64))
+    assert math.isclose(math.hypot(z0[0], z1[0]), math.sqrt(48 * math.log(2)), rel_tol=1e-12)
+
+
+def test_seed_key_splits_the_64_bit_seed():
+    for s in (0, 1, 0xFFFFFFFF, 0x100000000, 0xDEADBEEFCAFEF00D):
+        lo, hi = O.seed_key(s)
+        assert 0 <= lo < 2 ** 32 and 0 <= hi < 2 ** 32 and lo + (hi << 32) == s
+    assert O.seed_key(-1) == (0xFFFFFFFF, 0xFFFFFFFF)      # two's complement wrap
+
+
+def test_minibatch_obs_is_the_union_of_the_blocks():
+    """Brute force: block b holds canonical positions [b B, (b + 1) B), the last
+    block ragged; the minibatch is exactly the observations at those positions."""
+    rng = np.random.default_rng(3)
+    N, B = 23, 5
+    order = rng.permutation(N)
+    for blocks in ([4], [0, 2], [3, 1, 4], list(range(5)), []):
+        got = O.minibatch_obs(order, B, np.array(blocks, np.int64))
+        want = [int(order[p]) for p in range(N) if p // B in blocks]
+        assert sorted(got.tolist()) == sorted(want)
+    assert O.minibatch_obs(order, B, np.array([4])).size == 3
+
+
+def test_pair_table_and_homogeneous_travel_times_by_brute_force():
+    """Every observation's two nodes are its (event, station) pairs, each pair
+    met once, and T of a node is |x - s| / v0 for its own event and station."""
+    P = tiny_problem(M=9, S=3, K=3, seed=5)
+    sel = np.arange(0, P.N, 2)
+    ni, nj, nev, nst, T, dT = O.travel_times(P, P.init, sel)
+    pairs = {(int(P.i[o]), int(P.k[o])) for o in sel} | {(int(P.j[o]), int(P.k[o])) for o in sel}
+    assert len(nev) == len(pairs) and set(zip(nev.tolist(), nst.tolist())) == pairs
+    for a, o in enumerate(sel):
+        assert (nev[ni[a]], nst[ni[a]]) == (P.i[o], P.k[o])
+        assert (nev[nj[a]], nst[nj[a]]) == (P.j[o], P.k[o])
+    for n in range(len(nev)):
+        d = P.init[nev[n], :3] - P.stations[nst[n]]
+        assert math.isclose(T[n], math.sqrt(float(d @ d)) / 6.0, rel_tol=1e-14)
+
+
+def test_grad_norms_by_hand():
+    g = np.array([[1.0, 2.0, 2.0, 4.0], [0.0, 0.0, 0.0, 0.0], [3.0, 0.0, 4.0, 0.0], [-6.0, 0, 0, 8.0]])
+    assert O.grad_norms(g).tolist() == [5.0, 0.0, 5.0, 10.0]

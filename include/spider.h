@@ -309,8 +309,11 @@ int spider_debug_obs(spider_ctx *ctx, int64_t *idx_out, float *r_out, float *q_o
  * (0: it runs after them on the context's stream); knobs[5] (1, 2 (default)
  * or 4) threads per CTA of the per-block kernels (pair table, residuals,
  * whitened residuals), in units of 256 (the observations and nodes each thread
- * handles; changes only the rounding order of the FP64 log-likelihood sum).
- * Invalidates the captured step graph. */
+ * handles; changes only the rounding order of the FP64 log-likelihood sum);
+ * knobs[6] 1 (default): the size classes of the units' small inverses
+ * (piece blocks, then Schur complements) run side by side on four branch
+ * streams, 0: one after the other on the context's stream.  The first
+ * min(n, 7) knobs are set, the others kept.  Invalidates the captured step graph. */
 int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
 
 /* Facts about a context (synchronous), out[0..n): [0] sub-problems,

@@ -37,7 +37,7 @@ struct spider_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_ok = true;
   bool use_graph = true;
-  int32_t knobs[6] = {2, 1, 2, 1, 2, 2};   // see spider_set_tuning
+  int32_t knobs[7] = {2, 1, 2, 1, 2, 2, 1};   // see spider_set_tuning
   // whitening through precomputed piece inverses (minibatch steps)
   bool fast = false;               // tables built
   bool mb_full_sub = false;        // a sub-problem selects all its blocks in a minibatch
@@ -46,6 +46,7 @@ struct spider_ctx {
   int64_t piece_bytes = 0;
   cudaStream_t side = nullptr;     // second stream of the piece-inverse whitening
   cudaEvent_t fork = nullptr, join = nullptr;
+  Branches ubr{};                  // branch streams of the units' set-up
   int64_t n_samples = 0;           // samples written so far (ring of sample_cap)
   int64_t last_nb = 0;
   bool timing = false;
@@ -80,6 +81,20 @@ int cuda_fail(spider_ctx* c, cudaError_t e, const char* what) {
   if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
   g_static_err = cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? SPIDER_E_OOM : SPIDER_E_CUDA;
+}
+
+void destroy_branches(Branches& b) {
+  for (int i = 0; i < 4; ++i) {
+    if (b.s[i]) {
+      cudaStreamSynchronize(b.s[i]);
+      cudaStreamDestroy(b.s[i]);
+    }
+    if (b.join[i]) cudaEventDestroy(b.join[i]);
+    b.s[i] = nullptr;
+    b.join[i] = nullptr;
+  }
+  if (b.fork) cudaEventDestroy(b.fork);
+  b.fork = nullptr;
 }
 
 #define CK(ctx, call)                                   \
@@ -252,7 +267,8 @@ cudaError_t step_sequence(spider_ctx* c, int64_t n_b, bool logpost, bool timed, 
   TRY(launch_resid(v, n_b, c->gu, st, timed ? &c->ev[3] : nullptr, 256 * c->knobs[5]));
   if (fast) {
     TRY(launch_whiten_fast(v, n_b, c->cfg.pcg_tol, c->cc_grid, c->unit_grids, c->clean_grid, st, c->side,
-                           c->fork, c->join, timed ? c->wev : nullptr, c->knobs[4]));
+                           c->fork, c->join, timed ? c->wev : nullptr, c->knobs[4],
+                           c->knobs[6] ? &c->ubr : nullptr));
     StepView vg = v;
     vg.gate = v.wfast + kWGeneral;
     TRY(launch_pcg(vg, n_b, c->cfg.pcg_max_it, c->cfg.pcg_tol, c->pgrid, c->knobs[0], c->knobs[1], st));
@@ -491,6 +507,11 @@ int build_fast_whitening(spider_ctx* c, const Prep& P) {
   if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking))) return cuda_fail(c, e, "side stream");
   if ((e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming))) return cuda_fail(c, e, "event");
   if ((e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming))) return cuda_fail(c, e, "event");
+  if ((e = cudaEventCreateWithFlags(&c->ubr.fork, cudaEventDisableTiming))) return cuda_fail(c, e, "event");
+  for (int i = 0; i < 4; ++i) {
+    if ((e = cudaStreamCreateWithFlags(&c->ubr.s[i], cudaStreamNonBlocking))) return cuda_fail(c, e, "branch stream");
+    if ((e = cudaEventCreateWithFlags(&c->ubr.join[i], cudaEventDisableTiming))) return cuda_fail(c, e, "event");
+  }
   c->piece_bytes = bytes;
   c->fast = true;
   return SPIDER_OK;
@@ -518,6 +539,7 @@ int create_impl(const spider_catalog* cat, const spider_stations* sta, const spi
     if (c->side) cudaStreamDestroy(c->side);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
+    destroy_branches(c->ubr);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return code;
@@ -1218,14 +1240,14 @@ int spider_debug_obs(spider_ctx* c, int64_t* idx_out, float* r_out, float* q_out
 
 int spider_set_tuning(spider_ctx* c, const int32_t* knobs, int32_t n) {
   if (!c || (n > 0 && !knobs)) return SPIDER_E_INVAL;
-  const int32_t lo[6] = {1, 1, 1, 0, 0, 1}, hi[6] = {8, 4, 2, 1, 4, 4};
-  for (int32_t i = 0; i < n && i < 6; ++i)
+  const int32_t lo[7] = {1, 1, 1, 0, 0, 1, 0}, hi[7] = {8, 4, 2, 1, 4, 4, 1};
+  for (int32_t i = 0; i < n && i < 7; ++i)
     if (knobs[i] < lo[i] || knobs[i] > hi[i]) {
       c->err = "tuning knob out of range";
       return SPIDER_E_INVAL;
     }
   CK(c, cudaStreamSynchronize(c->stream));
-  for (int32_t i = 0; i < n && i < 6; ++i) {
+  for (int32_t i = 0; i < n && i < 7; ++i) {
     if (i == 5 && knobs[i] == 3) {
       c->err = "tuning knob out of range";
       return SPIDER_E_INVAL;
@@ -1317,6 +1339,7 @@ void spider_destroy(spider_ctx* c) {
   }
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
+  destroy_branches(c->ubr);
   free_all(c->allocs);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -977,29 +977,51 @@ cudaError_t configure_units_kernels() {
                               (int)(128 * 128 * sizeof(float)));
 }
 
-cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st, cudaEvent_t mid) {
+cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st, cudaEvent_t mid,
+                         const Branches* br) {
   const int gw = num_sms * 4;            // CTAs of the per-unit kernels (kUWarps warps each)
   const int gt = num_sms * 8;            // CTAs of the per-occurrence kernels
   int32_t* n_units = v.wfast + kWUnits;
+  cudaError_t e;
   k_u_prep<<<gw, kUWarps * 32, 0, st>>>(v);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_nocc, n_units, v.uocc_off, v.u_cap, v.wfast);
   k_u_occ<<<gw * (kUWarps / kUOccWarps), kUOccWarps * 32, 0, st>>>(v);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_gsz, n_units, v.u_goff, v.ginv_cap, v.wfast);
   k_u_scan<<<1, 1024, 0, st>>>(v.u_ssz, n_units, v.u_soff, v.sinv_cap, v.wfast);
   // (A_p[G,G])^-1 and S^-1 by size class: a warp per matrix in shared memory up
-  // to 32 nodes, a CTA per matrix in registers above (strips of 16 and 24 rows)
+  // to 32 nodes, a CTA per matrix in registers above (strips of 16 and 24 rows).
+  // The classes of one group take disjoint pieces (units) and write disjoint
+  // parts of the pools, so with branch streams they run side by side; every
+  // S^-1 waits for all the piece inverses.
+  auto fork = [&](int n) -> cudaError_t {
+    if (!br) return cudaSuccess;
+    cudaError_t r = cudaEventRecord(br->fork, st);
+    for (int i = 0; i < n && r == cudaSuccess; ++i) r = cudaStreamWaitEvent(br->s[i], br->fork, 0);
+    return r;
+  };
+  auto join = [&](int n) -> cudaError_t {
+    if (!br) return cudaSuccess;
+    cudaError_t r = cudaSuccess;
+    for (int i = 0; i < n && r == cudaSuccess; ++i) {
+      r = cudaEventRecord(br->join[i], br->s[i]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(st, br->join[i], 0);
+    }
+    return r;
+  };
+  auto lane = [&](int i) { return br ? br->s[i] : st; };
+  if ((e = fork(2)) != cudaSuccess) return e;
+  k_u_ginv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, lane(0)>>>(v);
+  k_u_ginv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, lane(1)>>>(v);
   k_u_ginv_w<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
-  k_u_ginv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, st>>>(v);
-  k_u_ginv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, st>>>(v);
+  if ((e = join(2)) != cudaSuccess) return e;
+  if ((e = fork(4)) != cudaSuccess) return e;
+  k_u_sinv_big<<<num_sms, 256, kUMaxGamma * kUMaxGamma * sizeof(float), lane(0)>>>(v);
+  k_u_sinv_d<96, 128, 32, 512, kWCursorS2><<<num_sms, 512, 128 * 128 * sizeof(float), lane(1)>>>(v);
+  k_u_sinv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, lane(2)>>>(v);
+  k_u_sinv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, lane(3)>>>(v);
   k_u_sinv_w<0, 32, 8><<<num_sms * 6, 256, 0, st>>>(v);
-  k_u_sinv<32, 64, 64, 16, 256, 1><<<num_sms * 6, 256, 0, st>>>(v);
-  k_u_sinv<64, 96, 96, 24, 384, 1><<<num_sms * 2, 384, 0, st>>>(v);
-  k_u_sinv_d<96, 128, 32, 512, kWCursorS2><<<num_sms, 512, 128 * 128 * sizeof(float), st>>>(v);
-  k_u_sinv_big<<<num_sms, 256, kUMaxGamma * kUMaxGamma * sizeof(float), st>>>(v);
-  if (mid) {
-    const cudaError_t e = cudaEventRecord(mid, st);
-    if (e != cudaSuccess) return e;
-  }
+  if ((e = join(4)) != cudaSuccess) return e;
+  if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;
   k_u_init<<<gt, kUTh, 0, st>>>(v);
   for (int r = 0; r < 2; ++r) {
     if (r > 0) {

@@ -917,7 +917,7 @@ int piece_cc_grid(int num_sms) {
 // solved on the side stream while the units are solved on st
 cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[4],
                                int clean_grid, cudaStream_t st, cudaStream_t side, cudaEvent_t fork,
-                               cudaEvent_t join, const cudaEvent_t* ev, int clean_share) {
+                               cudaEvent_t join, const cudaEvent_t* ev, int clean_share, const Branches* br) {
   if (!v.whiten) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(v.wfast, 0, kWSlots * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
@@ -945,7 +945,7 @@ cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc
     if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
   }
   // units: data-parallel, then the CTA passes for the units it handed over
-  e = launch_units(v, tol, grids[3], st, ev ? ev[1] : nullptr);
+  e = launch_units(v, tol, grids[3], st, ev ? ev[1] : nullptr, br);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   k_whiten_units<KW1><<<grids[1], 256, sizeof(Smem1), st>>>(v, tol);

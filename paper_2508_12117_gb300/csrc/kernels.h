@@ -49,15 +49,26 @@ cudaError_t configure_whiten_kernels();
 int whiten_units_grids(int num_sms, int grids[3]);
 int piece_cc_grid(int num_sms);
 int whiten_clean_grid(int num_sms);
-// the units of a step, data-parallel (k_units.cu)
-cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st, cudaEvent_t mid = nullptr);
+// branch streams on which independent kernels of one stage run side by side:
+// `fork` is recorded on the launching stream and waited on by each branch,
+// join[i] is recorded on branch i and waited on by the launching stream
+struct Branches {
+  cudaStream_t s[4];
+  cudaEvent_t fork;
+  cudaEvent_t join[4];
+};
+// the units of a step, data-parallel (k_units.cu); br (nullable): the size
+// classes of the small inverses run concurrently on its streams
+cudaError_t launch_units(const StepView& v, float tol, int num_sms, cudaStream_t st, cudaEvent_t mid = nullptr,
+                         const Branches* br = nullptr);
 cudaError_t configure_units_kernels();
 // ev (nullable): five events recorded on st after the piece labelling, the
 // units' set-up, their refinement rounds, the CTA unit passes and the join
 // with the clean-piece solver (timed evaluations only)
 cudaError_t launch_whiten_fast(const StepView& v, int64_t n_b, float tol, int cc_grid, const int grids[4],
                                int clean_grid, cudaStream_t st, cudaStream_t side, cudaEvent_t fork,
-                               cudaEvent_t join, const cudaEvent_t* ev = nullptr, int clean_share = 4);
+                               cudaEvent_t join, const cudaEvent_t* ev = nullptr, int clean_share = 4,
+                               const Branches* br = nullptr);
 // stage-1 outlier mask (k_outlier.cu)
 size_t outlier_scratch_bytes(int n_sub);
 cudaError_t launch_outlier(const StepView& v, int n_sub, float kmad, void* scratch, uint8_t* keep,

@@ -120,3 +120,33 @@ def test_dense_catalog_units_stay_on_the_data_parallel_path():
         assert info["fallback"] == 0 and handed == 0 and info["units"] > 0
         assert rel_g <= GRAD_TOL and rel_q <= GRAD_TOL and rel_lp <= 1e-5
     ctx.close()
+
+
+def test_concurrent_unit_setup_equals_the_serial_order():
+    """The size classes of the units' small inverses run side by side on branch
+    streams (knob 6 = 1, the default) or one after the other (0): the classes
+    take disjoint pieces and units, so gradients and SGLD chains (graph steps)
+    are bit-identical.  The dense catalog puts units in every class, up to ~190
+    shared nodes."""
+    s = synth.scaled_spec(3, 20000, batch_n=1 << 18)
+    cat = synth.make_catalog(s)
+    a = binding.Context.from_catalog(cat)
+    b = binding.Context.from_catalog(cat)
+    b.spider_set_tuning([2, 1, 2, 1, 2, 2, 0])
+    for seed in (1, 4):
+        ga, la = a.spider_grad_logpost(seed)
+        gb, lb = b.spider_grad_logpost(seed)
+        ia, ib = a.spider_info(), b.spider_info()
+        print(f"seed {seed}: units {ia['units']}, fallback {ia['fallback']} / {ib['fallback']}")
+        assert ia["units"] > 0 and ia["fallback"] == ib["fallback"]
+        assert np.array_equal(ga, gb) and la == lb
+    eps = s.hyper.eps
+    for k in range(4):
+        a.spider_sgld_step(eps, 40 + k)
+        b.spider_sgld_step(eps, 40 + k)
+    assert a.spider_info()["graph"] == 1 and b.spider_info()["graph"] == 1
+    ta, _ = a.spider_get_state()
+    tb, _ = b.spider_get_state()
+    assert np.array_equal(ta, tb) and np.isfinite(ta).all()
+    a.close()
+    b.close()

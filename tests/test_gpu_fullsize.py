@@ -1,0 +1,61 @@
+"""Parity at the full size of the 1M-event workload (1M events on 500 faults,
+200 stations, 200 M dd observations, 2^22-observation minibatches of 4096-obs
+blocks, MLP 6 -> 4x256 -> 1), in the launch configuration the benchmark times
+(a context per precision with the workload's default configuration).
+
+One minibatch of the step is checked against the FP64 oracle on all of its
+outputs (one oracle evaluation of it takes ~20 s on 16 cores): the selected
+blocks bit-exact and in order, the observation set, the whitened residuals
+q = Sigma^-1 r and the log-posterior gradient of every event; BF16 (the
+benchmark's form) at its stated tolerance and FP32 at 1e-5."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import spider_oracle as O
+from paper_2508_12117_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+SEED = 1_010_003
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def full():
+    t = time.time()
+    cat = synth.make_catalog(4)
+    P = O.problem_from_catalog(cat)
+    blocks = O.select_blocks(P.N, P.block_obs, P.batch_n, SEED)
+    sel = P.batch(SEED)
+    L, go, info = O.log_posterior(P, cat.init_xyzt, sel)
+    print(f"1M-event workload: {cat.M} events, {cat.N} obs, minibatch {sel.size} obs in {blocks.size} "
+          f"blocks; catalog + oracle {time.time() - t:.0f} s")
+    return cat, blocks, sel, L, go, info["q"]
+
+
+@pytest.mark.parametrize("prec,tol", [(binding.BF16, 5e-3), (binding.FP32, 1e-5)], ids=["bf16", "fp32"])
+def test_full_size_minibatch_matches_oracle(full, prec, tol):
+    cat, blocks, sel, L, go, qo = full
+    ctx = binding.Context.from_catalog(cat, precision=prec)
+    try:
+        g, lp = ctx.spider_grad_logpost(SEED)
+        got_blocks = ctx.spider_debug_blocks()
+        idx, _, q = ctx.spider_debug_obs(2 * sel.size)
+        info = ctx.spider_info()
+    finally:
+        ctx.close()
+    assert np.array_equal(got_blocks, blocks)                 # bit-exact selection, same order
+    assert idx.size == sel.size and np.array_equal(np.sort(idx), sel)
+    pos = np.searchsorted(sel, idx)
+    rel_g, rel_q = rel_l2(g, go), rel_l2(q, qo[pos])
+    print(f"precision {prec}: gradient rel-L2 {rel_g:.2e}, q rel-L2 {rel_q:.2e}, logpost {lp:.10e} vs "
+          f"{L:.10e}; units {info['units']}, fallback {info['fallback']}")
+    assert np.isfinite(g).all()
+    assert rel_g <= tol and rel_q <= tol
+    if prec == binding.FP32:
+        assert abs(lp - L) <= 1e-5 * abs(L)

@@ -7,7 +7,9 @@ One minibatch of the step is checked against the FP64 oracle on all of its
 outputs (one oracle evaluation of it takes ~20 s on 16 cores): the selected
 blocks bit-exact and in order, the observation set, the whitened residuals
 q = Sigma^-1 r and the log-posterior gradient of every event; BF16 (the
-benchmark's form) at its stated tolerance and FP32 at 1e-5."""
+benchmark's form) at its stated tolerance and FP32 at 1e-5.  Then one SGLD
+step through the captured graph: the update of that gradient with the
+oracle's Philox noise, within 1 mm."""
 import time
 
 import numpy as np
@@ -47,6 +49,12 @@ def test_full_size_minibatch_matches_oracle(full, prec, tol):
         got_blocks = ctx.spider_debug_blocks()
         idx, _, q = ctx.spider_debug_obs(2 * sel.size)
         info = ctx.spider_info()
+        # one SGLD step (captured graph, the benchmark's launch path) from the
+        # same state with the same seed: same minibatch, same Philox noise
+        eps = cat.spec.hyper.eps
+        ctx.spider_sgld_step(eps, SEED)
+        th, step = ctx.spider_get_state()
+        graph = ctx.spider_info()["graph"]
     finally:
         ctx.close()
     assert np.array_equal(got_blocks, blocks)                 # bit-exact selection, same order
@@ -59,3 +67,18 @@ def test_full_size_minibatch_matches_oracle(full, prec, tol):
     assert rel_g <= tol and rel_q <= tol
     if prec == binding.FP32:
         assert abs(lp - L) <= 1e-5 * abs(L)
+    # the step is the update of Sec. 3.2 with the gradient just checked and the
+    # oracle's Philox noise: theta0 + eps g + sqrt(2 eps) eta, to FP32 rounding
+    # of the increment.  From the perturbed start the drift moves events up to
+    # ~36 m and the noise up to ~3 m, so a dropped or misindexed term fails.
+    eta = O.langevin_noise(cat.M, SEED)
+    want = O.sgld_update(cat.init_xyzt, g.astype(np.float64), eps, eta)
+    dx_m = float(np.abs(th[:, :3] - want[:, :3]).max() * 1e3)
+    dt_ms = float(np.abs(th[:, 3] - want[:, 3]).max() * 1e3)
+    to = O.sgld_update(cat.init_xyzt, go, eps, eta)
+    vs_oracle_m = float(np.abs(th[:, :3] - to[:, :3]).max() * 1e3)
+    moved_m = float(np.abs(to[:, :3] - cat.init_xyzt[:, :3]).max() * 1e3)
+    print(f"one SGLD step: max |dx| {dx_m:.2e} m, |dt0| {dt_ms:.2e} ms from the update with the device "
+          f"gradient; {vs_oracle_m:.2e} m from the oracle's step (which moves events up to {moved_m:.1f} m)")
+    assert step == 1 and graph == 1
+    assert dx_m <= 1e-3 and dt_ms <= 1e-3

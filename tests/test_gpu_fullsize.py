@@ -28,14 +28,25 @@ def rel_l2(a, b):
 
 
 def _host_gb_available():
+    """Free host memory in GB: MemAvailable, capped by the cgroup's limit."""
+    gb = float("inf")
     try:
         with open("/proc/meminfo") as f:
             for line in f:
                 if line.startswith("MemAvailable:"):
-                    return int(line.split()[1]) / 1e6
+                    gb = int(line.split()[1]) / 1e6
     except OSError:
         pass
-    return float("inf")
+    try:
+        with open("/sys/fs/cgroup/memory.max") as f:
+            lim = f.read().strip()
+        with open("/sys/fs/cgroup/memory.current") as f:
+            cur = int(f.read().strip())
+        if lim != "max":
+            gb = min(gb, (int(lim) - cur) / 1e9)
+    except (OSError, ValueError):
+        pass
+    return gb
 
 
 @pytest.fixture(scope="module")

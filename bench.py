@@ -605,7 +605,7 @@ def main():
         line = run_ours(args, rank, world)
         if line is not None:
             cat = line.pop("_cat")
-            if not args.no_cpu_baseline:
+            if not args.no_cpu_baseline and world == 1:     # the oracle baseline: rank 0 at N = 1
                 base, _ = oracle_step(cat, 1_000_003 + 10_000)
                 line["cpu_baseline"] = base
     if line is not None:

@@ -326,10 +326,10 @@ int spider_set_tuning(spider_ctx *ctx, const int32_t *knobs, int32_t n);
  * shared nodes in the last such step, [12] 1 if that step fell back to the
  * general component solver (a unit beyond the limits of the direct path),
  * [13] units of that step solved by the last unit pass, [14], [15] SM cycles /
- * 1024 spent on the units of the CTA pass and of the last pass, [16..30] per
- * unit pass (one warp, CTA, last) five counters: SM cycles / 1024 in set-up,
- * the pieces' small inverses, the inverse of S, the refinement rounds, and
- * the units solved; [31..37] units the data-parallel unit solver handed to
+ * 1024 spent on the units of the CTA pass and of the last pass, [16..30]
+ * five counters per unit pass ([16..20] stay zero; [21..25] the CTA pass,
+ * [26..30] the last pass): SM cycles / 1024 in set-up, the pieces' small
+ * inverses, the inverse of S, the refinement rounds, and the units solved; [31..37] units the data-parallel unit solver handed to
  * the CTA passes since the context was created, by reason: too many pieces,
  * shared occurrences, shared nodes, shared nodes of one piece, a failed small
  * inverse, a failed inverse of S, a full pool; [38] kernel launches in the

@@ -317,9 +317,9 @@ __global__ void __launch_bounds__(kCleanWarps * 32) k_whiten_clean(StepView v, f
 }
 
 // ------------------------------------------------------------------ units
-// Three passes over the units, each deferring what exceeds its shared memory to
-// the next: one warp per unit (most units: a few pieces, tens of shared nodes),
-// then 256-thread CTAs, two per SM (S^-1 of up to 64 shared nodes in shared
+// Two CTA passes over the units the data-parallel unit solver (k_units.cu)
+// handed over, the first deferring what exceeds its shared memory to the
+// second: 256-thread CTAs, two per SM (S^-1 of up to 64 shared nodes in shared
 // memory), then one CTA per SM (up to 160; beyond that the CTA's global
 // scratch holds S^-1 and the pieces' small inverses).
 template <int PC, int OCC, int GAM, int SMG, int SMGINV>
@@ -444,23 +444,23 @@ __device__ void cta_exscan(int n, F flag_of, int* pre_out, int32_t* sm, int32_t*
   __syncthreads();
 }
 
-// MODE 0: every unit, one warp each; MODE 1: the units MODE 0 deferred;
-// MODE 2: the units MODE 1 deferred (the last pass: S^-1 and the small
-// inverses go to global scratch when they exceed its shared memory, and a unit
-// beyond PC, OCC or GAM hands the step to the general solver).
+// MODE 1: the units the data-parallel solver handed over; MODE 2: the units
+// MODE 1 deferred (the last pass: S^-1 and the small inverses go to global
+// scratch when they exceed its shared memory, and a unit beyond PC, OCC or GAM
+// hands the step to the general solver).
 template <int PC, int OCC, int GAM, int SMG, int SMGINV, int NT, int MODE>
 __global__ void __launch_bounds__(NT) k_whiten_units(StepView v, float tol) {
+  static_assert(MODE == 1 || MODE == 2, "unit pass");
   extern __shared__ __align__(16) uint8_t smu[];
   using Smem = UnitSmem<PC, OCC, GAM, SMG, SMGINV>;
   Smem& S = *reinterpret_cast<Smem*>(smu);
   if (aborted_cta(v)) return;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const float lam = v.lam;
-  const int32_t nu = MODE == 0 ? v.wfast[kWUnits] : (MODE == 1 ? v.wfast[kWDefer] : v.wfast[kWDefer2]);
+  const int32_t nu = MODE == 1 ? v.wfast[kWDefer] : v.wfast[kWDefer2];
   // the pass's deferral: the next pass's list, or the general solver after the last
   auto defer = [&](int32_t unit) {
-    if (MODE == 0) v.unit_defer[atomicAdd(&v.wfast[kWDefer], 1)] = unit;
-    else if (MODE == 1) v.unit_defer2[atomicAdd(&v.wfast[kWDefer2], 1)] = unit;
+    if (MODE == 1) v.unit_defer2[atomicAdd(&v.wfast[kWDefer2], 1)] = unit;
     else atomicExch(&v.wfast[kWGeneral], 1);
   };
   float* const s_glob = v.wscratch + (int64_t)blockIdx.x * kUScratch;   // S^-1 when it is large
@@ -468,10 +468,10 @@ __global__ void __launch_bounds__(NT) k_whiten_units(StepView v, float tol) {
   int max_rounds = 0;
   for (;;) {
     __syncthreads();
-    if (tid == 0) S.cnt = atomicAdd(&v.wfast[MODE == 0 ? kWCursor0 : (MODE == 1 ? kWCursor : kWCursor2)], 1);
+    if (tid == 0) S.cnt = atomicAdd(&v.wfast[MODE == 1 ? kWCursor : kWCursor2], 1);
     __syncthreads();
     if (S.cnt >= nu) break;
-    const int32_t u = MODE == 0 ? S.cnt : (MODE == 1 ? v.unit_defer[S.cnt] : v.unit_defer2[S.cnt]);
+    const int32_t u = MODE == 1 ? v.unit_defer[S.cnt] : v.unit_defer2[S.cnt];
     const long long t_unit = clock64();
     int32_t* const dbg = v.wfast + kWSlots + 64 + MODE * 5;
     long long t_ph = t_unit;
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(NT) k_whiten_units(StepView v, float tol) {
     if (tid == 0) atomicAdd(&dbg[4], 1);
     if (tid == 0) {
       if (MODE == 2) atomicAdd(&v.wfast[kWBigS], 1);
-      atomicAdd(&v.wfast[MODE == 0 ? kWCycW : (MODE == 1 ? kWCycSm : kWCycBig)],
+      atomicAdd(&v.wfast[MODE == 1 ? kWCycSm : kWCycBig],
                 (int)((clock64() - t_unit) >> 10));
     }
     for (int o = tid; o < nocc; o += nt)

@@ -203,7 +203,7 @@ struct StepView {
   int32_t* unit_off;              // [G + 1]
   int32_t* unit_pieces;           // [G]
   int32_t* unit_pblk;             // [G]: block of each entry of unit_pieces
-  int32_t* unit_defer;            // [G]: units deferred from the one-warp pass to the CTA pass
+  int32_t* unit_defer;            // [G]: units the data-parallel solver handed to the CTA pass
   int32_t* unit_defer2;           // [G]: units deferred from the CTA pass to the last pass
   int32_t* clean_list;            // [G]: pieces of the step with no shared node
   int32_t* clean_blk;             // [G]: their blocks
@@ -250,9 +250,8 @@ enum : int {
   kWCursor2 = 8,   // work cursor of the second pass
   kWClean = 9,     // single pieces of the step (no shared node)
   kWCursorC = 10,  // work cursor of the single-piece solver
-  kWCursor0 = 11,  // work cursor of the one-warp unit pass
+  // slots 11 and 13: unused
   kWDefer2 = 12,   // units deferred from the CTA pass to the last pass
-  kWCycW = 13,     // SM cycles / 1024 spent on units of the one-warp pass
   kWCursorS = 14,  // work cursor of the CTA inverse of the largest S
   kWCursorS2 = 15, // work cursor of the register inverse of S at 97..128 shared nodes
   kWSlots = 16

@@ -568,6 +568,9 @@ def oracle_step(cat, seed):
                        f"{hc['nproc']} threads; set-up {t_setup:.1f} s not counted")}, per
 
 
+REFERENCE_BUDGET_S = 90.0      # wall time the reference arm's timed steps may take
+
+
 def run_reference(args, rank, world):
     """The oracle's SGLD chain on the workload: up to --warmup untimed steps (at
     least one, none started after a sixth of REFERENCE_BUDGET_S), then up
